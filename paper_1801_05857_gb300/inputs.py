@@ -1,0 +1,277 @@
+"""Seeded synthetic inputs: networks of LTSs and key sequences.
+
+This module only *draws* inputs. It holds none of the exploration arithmetic
+(no successor generation, no packing, no hashing of states), so the CPU oracle
+and the CUDA path can both be fed from it without sharing any of the method.
+
+A network (Sec. 3, Fig. 1) is a list of process LTSs -- each a set of local
+states, an initial state and labelled edges -- plus synchronisation rules.  A
+rule lists (process, label) participants; those participants move together,
+and a label that a process uses in some rule never fires alone in that
+process.  Every other (process, label) pair interleaves.
+
+Randomness comes from a splitmix64 stream (Steele, Lea & Flood, "Fast
+splittable pseudorandom number generators", OOPSLA 2014), written out in plain
+Python integers so that the same seed gives the same network on any machine.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+M64 = (1 << 64) - 1
+
+
+class SplitMix64:
+    """splitmix64 generator: state += golden gamma, then the two-multiply finaliser."""
+
+    def __init__(self, seed: int):
+        self.state = seed & M64
+
+    def next(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & M64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+        return z ^ (z >> 31)
+
+    def below(self, n: int) -> int:
+        """Uniform-ish integer in [0, n) (modulo bias < n / 2^64)."""
+        return self.next() % n
+
+    def between(self, lo: int, hi: int) -> int:
+        """Integer in [lo, hi] inclusive."""
+        return lo + self.below(hi - lo + 1)
+
+    def sample(self, n: int, k: int) -> list[int]:
+        """k distinct values from range(n), partial Fisher-Yates."""
+        pool = list(range(n))
+        for i in range(k):
+            j = i + self.below(n - i)
+            pool[i], pool[j] = pool[j], pool[i]
+        return pool[:k]
+
+
+def substream(seed: int, *path: int) -> SplitMix64:
+    """Independent stream for (seed, path...): each component is folded through one draw."""
+    g = SplitMix64(seed)
+    s = g.next()
+    for p in path:
+        s = SplitMix64(s ^ ((p + 1) * 0xD1B54A32D192ED03 & M64)).next()
+    return SplitMix64(s)
+
+
+@dataclass
+class LTS:
+    n_states: int
+    initial: int
+    edges: list  # list of (src, label, dst)
+
+
+@dataclass
+class Rule:
+    parts: list  # list of (proc, label); processes are distinct
+    result: int = 0
+
+
+@dataclass
+class Network:
+    n_labels: int
+    procs: list
+    rules: list = field(default_factory=list)
+    name: str = ""
+
+    @property
+    def n_procs(self) -> int:
+        return len(self.procs)
+
+    def flat(self) -> dict:
+        """Plain arrays for marshalling across a C boundary.
+
+        edges[e] = (src, label, dst) with process p's edges in
+        edges[edge_off[p]:edge_off[p+1]]; rule r's participants are
+        rule_parts[rule_off[r]:rule_off[r+1]] as (proc, label) rows.
+        """
+        n = self.n_procs
+        n_states = np.array([p.n_states for p in self.procs], dtype=np.uint32)
+        initial = np.array([p.initial for p in self.procs], dtype=np.uint32)
+        edge_off = np.zeros(n + 1, dtype=np.uint32)
+        rows = []
+        for i, p in enumerate(self.procs):
+            rows.extend(p.edges)
+            edge_off[i + 1] = edge_off[i] + len(p.edges)
+        edges = np.array(rows, dtype=np.uint32).reshape(-1, 3)
+        rule_off = np.zeros(len(self.rules) + 1, dtype=np.uint32)
+        parts = []
+        for r, rule in enumerate(self.rules):
+            parts.extend(rule.parts)
+            rule_off[r + 1] = rule_off[r] + len(rule.parts)
+        rule_parts = np.array(parts, dtype=np.uint32).reshape(-1, 2)
+        rule_result = np.array([r.result for r in self.rules], dtype=np.uint32)
+        return dict(n_procs=n, n_labels=self.n_labels, n_states=n_states, initial=initial,
+                    edge_off=edge_off, edges=np.ascontiguousarray(edges),
+                    rule_off=rule_off, rule_parts=np.ascontiguousarray(rule_parts),
+                    rule_result=rule_result)
+
+
+# --------------------------------------------------------------------------------------------
+# Hand-written networks
+# --------------------------------------------------------------------------------------------
+
+def producer_consumers() -> Network:
+    """The producer / two consumers network of Fig. 1.
+
+    Labels: 0 gen_work, 1 send, 2 rec, 3 work, 4 tau, 5 trans.
+    Producer: p0 -gen_work-> p1, p1 -send-> p0.
+    Consumer: c0 -rec-> c1, c1 -work-> c1, c1 -tau-> c0.
+    Rules: send * rec * _ -> trans and send * _ * rec -> trans.
+    """
+    producer = LTS(2, 0, [(0, 0, 1), (1, 1, 0)])
+    consumer = lambda: LTS(2, 0, [(0, 2, 1), (1, 3, 1), (1, 4, 0)])
+    rules = [Rule([(0, 1), (1, 2)], 5), Rule([(0, 1), (2, 2)], 5)]
+    return Network(6, [producer, consumer(), consumer()], rules, name="fig1_producer_consumers")
+
+
+def token_ring(n_nodes: int) -> Network:
+    """A ring of n nodes passing one token forward (Sec. 5.2 describes the model only in words).
+
+    Each node has two communication transitions (receive from the left
+    neighbour, send to the right one) and three internal transitions:
+      idle states i0 -> i1 -> i2 (two internal steps),
+      i2 -recv-> h0 (token arrives), h0 -> h1 (internal), h1 -send-> i0.
+    Local state numbering: i0=0, i1=1, i2=2, h0=3, h1=4 (3 bits per node).
+    Node 0 starts holding the token in h0, all others in i0.
+    Label 2k+0 is node k's internal step label, one 'pass_k' label per link
+    k -> k+1 is shared by node k (send) and node k+1 (recv) through a 2-party rule.
+    """
+    assert n_nodes >= 2
+    tau = 0
+    procs = []
+    for k in range(n_nodes):
+        send = 1 + k                      # link k -> k+1
+        recv = 1 + (k - 1) % n_nodes      # link k-1 -> k
+        edges = [(0, tau, 1), (1, tau, 2), (3, tau, 4), (2, recv, 3), (4, send, 0)]
+        procs.append(LTS(5, 3 if k == 0 else 0, edges))
+    rules = [Rule([(k, 1 + k), ((k + 1) % n_nodes, 1 + k)], 1 + k) for k in range(n_nodes)]
+    return Network(1 + n_nodes, procs, rules, name=f"token_ring_{n_nodes}")
+
+
+# --------------------------------------------------------------------------------------------
+# Random networks
+# --------------------------------------------------------------------------------------------
+
+def random_lts(rng: SplitMix64, n_states: int, deg_lo: int, deg_hi: int, labels: list,
+               initial: int = 0, cluster: int = 0, free_labels=()) -> LTS:
+    """Each state gets U{deg_lo..deg_hi} distinct (label, dst) edges, label uniform over `labels`.
+
+    With cluster > 0 the states form consecutive blocks of `cluster` states;
+    an edge stays inside its source's block unless its label is in
+    `free_labels`, in which case its destination is uniform over all states.
+    """
+    edges = []
+    for s in range(n_states):
+        d = rng.between(deg_lo, deg_hi)
+        seen = set()
+        while len(seen) < d:
+            a = labels[rng.below(len(labels))]
+            if cluster and a not in free_labels:
+                base = (s // cluster) * cluster
+                t = base + rng.below(min(cluster, n_states - base))
+            else:
+                t = rng.below(n_states)
+            if (a, t) not in seen:
+                seen.add((a, t))
+                edges.append((s, a, t))
+    return LTS(n_states, initial, edges)
+
+
+def random_network(seed: int, n_procs: int, n_states, deg_lo: int = 1, deg_hi: int = 3,
+                   n_labels: int = 6, n_sync: int = 2, parties: int = 2,
+                   sync_weight: float = 1.0, cluster: int = 0, name: str = "") -> Network:
+    """Random network in the style of the paper's benchmark models.
+
+    * n_states: int or a list with one entry per process.
+    * Labels 0..n_sync-1 synchronise: label a gets one rule over `parties`
+      distinct processes chosen once (a fixed rendezvous group); the others
+      are local.
+    * cluster > 0: local edges stay inside blocks of `cluster` consecutive
+      states and only synchronised edges lead out of a block, so rules gate
+      how far each process can wander (this is what keeps the product small
+      enough to enumerate).
+    * sync_weight scales how often a process picks, for an edge, one of the
+      sync labels it takes part in, relative to a local label (1.0 = uniform
+      over all labels it may use).  A process only draws labels that are
+      local or that it shares through a rule.
+    """
+    sizes = list(n_states) if isinstance(n_states, (list, tuple)) else [n_states] * n_procs
+    top = substream(seed, 0)
+    rules = []
+    member = [[] for _ in range(n_procs)]
+    for a in range(n_sync):
+        ps = sorted(top.sample(n_procs, parties))
+        rules.append(Rule([(p, a) for p in ps], a))
+        for p in ps:
+            member[p].append(a)
+    local = list(range(n_sync, n_labels))
+    procs = []
+    for p in range(n_procs):
+        rng = substream(seed, 1, p)
+        mine = member[p]
+        if sync_weight == 1.0 or not mine:
+            pool = local + mine
+        else:
+            # integer weights: repeat labels so the draw stays a plain uniform pick
+            w_sync = max(1, int(round(sync_weight * 4)))
+            pool = local * 4 + mine * w_sync
+        procs.append(random_lts(rng, sizes[p], deg_lo, deg_hi, pool, cluster=cluster,
+                                free_labels=set(mine)))
+    return Network(n_labels, procs, rules, name=name or f"random_s{seed}_n{n_procs}")
+
+
+def no_sync_network(seed: int, n_procs: int, n_states: int, deg_lo: int = 0, deg_hi: int = 2,
+                    n_labels: int = 4) -> Network:
+    """Random network without rules; deg_lo = 0 allows local sink states (deadlocks)."""
+    procs = []
+    for p in range(n_procs):
+        rng = substream(seed, 2, p)
+        procs.append(random_lts(rng, n_states, deg_lo, deg_hi, list(range(n_labels))))
+    return Network(n_labels, procs, [], name=f"nosync_s{seed}_n{n_procs}")
+
+
+# --------------------------------------------------------------------------------------------
+# Key sequences for the isolated hash-table experiment (Sec. 5.1)
+# --------------------------------------------------------------------------------------------
+
+def _mix31(i: np.ndarray, seed: int) -> np.ndarray:
+    """Bijection on [0, 2^31): odd multiply and xor-shifts, each invertible mod 2^31."""
+    m = np.uint64((1 << 31) - 1)
+    x = (i.astype(np.uint64) + np.uint64(seed & 0x7FFFFFFF)) & m
+    for mul in (0x2C1B3C6D, 0x297A2D39, 0x7FEB352D):
+        x = (x * np.uint64(mul | 1)) & m
+        x ^= x >> np.uint64(15)
+    return x
+
+
+def key_sequence(n: int, duplication: int, words: int = 1, seed: int = 0) -> np.ndarray:
+    """n keys of `words` uint32 each, n // duplication distinct ones, each repeated
+    `duplication` times, in a seeded random order (the paper's Sec. 5.1 input).
+
+    Keys are nonzero and keep bit 31 of every word clear.  Distinctness comes
+    from a bijection of the unique index in word 0, so no duplicates can
+    arise by chance.  Returns a (n, words) uint32 array (n must be a multiple
+    of duplication).
+    """
+    assert n % duplication == 0
+    u = n // duplication
+    idx = np.arange(u, dtype=np.uint64)
+    w0 = _mix31(idx, seed)
+    # the bijection sends exactly one index to 0; give that key the image of u instead,
+    # which no index below u can have
+    w0 = np.where(w0 == 0, _mix31(np.array([u], dtype=np.uint64), seed)[0], w0)
+    cols = [w0.astype(np.uint32)]
+    for k in range(1, words):
+        cols.append(_mix31(idx, seed * 7919 + 104729 * k).astype(np.uint32))
+    uniq = np.stack(cols, axis=1)
+    order = np.random.Generator(np.random.PCG64(seed)).permutation(n) % u
+    return np.ascontiguousarray(uniq[order])

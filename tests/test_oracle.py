@@ -1,0 +1,227 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+* Fig. 1's network has 8 states and 24 transitions (Sec. 3).
+* Our token ring reproduces every Token Ring count of Table 1 (Sec. 5.2) and
+  the transition count derived below.
+* Without rules the product's reachable set, transitions, BFS level sizes and
+  deadlocks have closed forms in per-process quantities.
+* On tiny networks with rules, the oracle agrees with a brute force that
+  writes the product as a sum of Kronecker products over the whole product
+  space (oracle/product_matrix.py) -- a different formulation of the same
+  semantics, not a second copy of the successor enumeration.
+* The state digest's mixer is splitmix64, whose first output from seed 0 is
+  the published value 0xE220A8397B1DCDAF.
+"""
+import json
+import os
+from collections import deque
+from itertools import product
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import product_matrix as pm
+from paper_1801_05857_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def golden(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+def test_splitmix64_published_first_output():
+    # splitmix64 seeded with 0 first returns 0xE220A8397B1DCDAF (Steele, Lea & Flood 2014;
+    # the reference sequence of the algorithm).  The oracle's digest of the one-process
+    # state (0,) is exactly that first output.
+    assert oracle.state_digest([0]) == 0xE220A8397B1DCDAF
+    assert inputs.SplitMix64(0).next() == 0xE220A8397B1DCDAF
+
+
+def test_fig1_counts():
+    g = golden("fig1_producer_consumers.json")
+    r = oracle.explore(inputs.producer_consumers())
+    assert r.states == g["states"]
+    assert r.transitions == g["transitions"]
+    assert r.deadlock_count == 0 and r.complete
+    assert sum(r.levels) == r.states
+
+
+def test_fig1_readings_that_the_counts_exclude():
+    """The two other readings of Sec. 3 give other counts: letting rule labels also
+    fire alone gives 36 transitions, and counting distinct (s, a, t) edges gives 22.
+    The oracle's reading is the only one that yields the published 24."""
+    net = inputs.producer_consumers()
+    t = pm.transition_matrix(net).toarray()
+    r = oracle.explore(net)
+    reach = pm.explore(net)["reachable"]
+    states = pm.states_of(net, reach)
+    # rule labels firing alone as well (the reachable set stays all 8 states): count the
+    # rule-labelled edges enabled in each state as extra single-process moves
+    extra = 0
+    for st in states:
+        for p in range(net.n_procs):
+            rl = {a for rule in net.rules for (q, a) in rule.parts if q == p}
+            extra += sum(1 for (s, lab, d) in net.procs[p].edges if s == st[p] and lab in rl)
+    assert r.transitions + extra == 36
+    # distinct (source, target) pairs: two consumers' 'work' self-loops in the same global
+    # state are one edge (s, work, s) when edges are not counted with multiplicity
+    distinct = set()
+    for st in states:
+        for succ in oracle.successors(net, st):
+            distinct.add((tuple(st), tuple(succ)))
+    assert len(distinct) == 22
+    assert int(t[np.ix_(reach, reach)].sum()) == 24
+
+
+@pytest.mark.parametrize("n_nodes", list(range(2, 12)))
+def test_token_ring_table1(n_nodes):
+    g = golden("token_ring_table1.json")
+    r = oracle.explore(inputs.token_ring(n_nodes))
+    assert r.states == g["states"][str(n_nodes)]
+    # Derivation: a global state is (token holder k, holder state h0|h1, the other
+    # N-1 nodes each in i0|i1|i2), all reachable: 2N 3^(N-1) states.  Enabled moves:
+    # each non-holder not at i2 steps (2/3 of them on average), the holder in h0 steps,
+    # the holder in h1 passes the token iff its right neighbour is at i2.  Summing,
+    # T = N * (4(N-1) 3^(N-2) + 3^(N-1) + 3^(N-2)) = 4 N^2 3^(N-2).
+    assert r.transitions == 4 * n_nodes * n_nodes * 3 ** (n_nodes - 2)
+    assert r.deadlock_count == 0 and r.complete
+    assert sum(r.levels) == r.states
+
+
+def _local_facts(lts):
+    """Per-process BFS: depth of every reachable local state."""
+    depth = {lts.initial: 0}
+    q = deque([lts.initial])
+    adj = {}
+    for (s, a, t) in lts.edges:
+        adj.setdefault(s, []).append(t)
+    while q:
+        s = q.popleft()
+        for t in adj.get(s, []):
+            if t not in depth:
+                depth[t] = depth[s] + 1
+                q.append(t)
+    deg = {s: len(adj.get(s, [])) for s in depth}
+    return depth, deg
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_no_sync_closed_forms(seed):
+    net = inputs.no_sync_network(seed, n_procs=5, n_states=6, deg_lo=0, deg_hi=3)
+    facts = [_local_facts(p) for p in net.procs]
+    sizes = [len(d) for d, _ in facts]
+    states = int(np.prod(sizes))
+    trans = 0
+    for p, (d, deg) in enumerate(facts):
+        trans += sum(deg.values()) * int(np.prod([sizes[q] for q in range(len(sizes)) if q != p]))
+    poly = np.array([1], dtype=object)
+    for d, _ in facts:
+        pp = np.zeros(max(d.values()) + 1, dtype=object)
+        for s, k in d.items():
+            pp[k] += 1
+        poly = np.convolve(poly, pp)
+    sinks = [[s for s, k in deg.items() if k == 0] for _, deg in facts]
+    dead = list(product(*sinks))
+    r = oracle.explore(net)
+    assert r.states == states
+    assert r.transitions == trans
+    assert r.levels == [int(x) for x in poly]
+    assert r.deadlock_count == len(dead)
+    hs = [oracle.state_digest(list(s)) for s in dead]
+    assert r.deadlock_sum == sum(hs) % (1 << 64)
+    x = 0
+    for h in hs:
+        x ^= h
+    assert r.deadlock_xor == x
+    # digest of the whole reachable set: the product of the local reachable sets
+    allh = [oracle.state_digest(list(s)) for s in product(*[sorted(d) for d, _ in facts])]
+    assert r.set_sum == sum(allh) % (1 << 64)
+
+
+def _tiny_sync_networks():
+    nets = [inputs.producer_consumers(), inputs.token_ring(3), inputs.token_ring(4)]
+    for seed in range(8):
+        nets.append(inputs.random_network(seed, 4, 5, 0, 3, 6, n_sync=2, parties=2))
+    for seed in range(4):
+        nets.append(inputs.random_network(100 + seed, 4, 4, 1, 3, 5, n_sync=2, parties=3))
+    nets.append(inputs.random_network(0, 4, 8, 1, 3, 6, n_sync=2, parties=2))  # tiny config shape
+    return nets
+
+
+@pytest.mark.parametrize("net", _tiny_sync_networks(), ids=lambda n: n.name)
+def test_oracle_matches_kronecker_brute_force(net):
+    bf = pm.explore(net)
+    r = oracle.explore(net, deadlocks_cap=1 << 16)
+    states, dist = oracle.deadlock_distances(net)
+    assert r.states == len(bf["reachable"])
+    got = {pm.index_of(net, s) for s in states}
+    assert got == set(int(i) for i in bf["reachable"])
+    assert r.levels == bf["levels"]
+    assert r.transitions == bf["transitions"]
+    assert r.deadlock_count == len(bf["deadlocks"])
+    assert {pm.index_of(net, s) for s in r.deadlocks} == set(int(i) for i in bf["deadlocks"])
+    assert (dist == 0).sum() == len(bf["deadlocks"])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_deadlock_distances_are_backward_bfs(seed):
+    net = inputs.random_network(seed, 4, 5, 0, 2, 6, n_sync=2, parties=2)
+    states, dist = oracle.deadlock_distances(net)
+    idx = {tuple(s): i for i, s in enumerate(states)}
+    inf = np.iinfo(np.uint32).max
+    for i, s in enumerate(states):
+        succ = oracle.successors(net, s)
+        if len(succ) == 0:
+            assert dist[i] == 0
+            continue
+        best = min(int(dist[idx[tuple(t)]]) for t in succ)
+        assert dist[i] == (inf if best == inf else best + 1)
+
+
+def test_stop_at_first_deadlock_finishes_that_level():
+    for seed in range(20):
+        net = inputs.random_network(seed, 4, 5, 0, 2, 6, n_sync=2, parties=2)
+        full = oracle.explore(net)
+        if full.deadlock_count == 0:
+            continue
+        first = oracle.explore(net, stop_at_first_deadlock=True)
+        k = first.first_deadlock_level
+        assert k == full.first_deadlock_level
+        assert first.levels[:k + 1] == full.levels[:k + 1]
+        assert first.explored == sum(full.levels[:k + 1])
+        # every deadlock of level k is found, and only those: the brute force's
+        # deadlocks whose BFS depth (matrix-step distance) is k
+        bf = pm.explore(net)
+        t = pm.transition_matrix(net).transpose().tocsr()
+        depth = {}
+        front = {pm.index_of(net, [p.initial for p in net.procs])}
+        d = 0
+        while front:
+            for i in front:
+                depth[i] = d
+            nxt = set()
+            for i in front:
+                v = np.zeros(t.shape[0], dtype=np.int64)
+                v[i] = 1
+                nxt |= set(np.flatnonzero(t @ v).tolist())
+            front = nxt - set(depth)
+            d += 1
+        want = {int(i) for i in bf["deadlocks"] if depth[int(i)] == k}
+        assert {pm.index_of(net, s) for s in first.deadlocks} == want
+        assert first.deadlock_count == len(want)
+        return
+    pytest.fail("no seed produced a deadlock")
+
+
+def test_key_sequence_duplication():
+    for d in (1, 2, 5, 21):
+        keys = inputs.key_sequence(2100, d, words=1, seed=3)
+        u, c = np.unique(keys[:, 0], return_counts=True)
+        assert len(u) == 2100 // d and (c == d).all()
+        assert (keys != 0).all() and ((keys >> 31) == 0).all()
+    k4 = inputs.key_sequence(1000, 4, words=4, seed=1)
+    u = np.unique(k4, axis=0)
+    assert len(u) == 250 and ((k4 >> 31) == 0).all()
