@@ -1,0 +1,228 @@
+/*
+ * gx -- breadth-first exploration of a network of synchronising LTSs on one
+ * GB300 GPU, with a warp-cooperative bucketed find-or-put hash table.
+ *
+ * The method is the one of "On the Scalability of the GPUexplore
+ * Explicit-State Model Checker" (Cassee, Neele, Wijs): a network of labelled
+ * transition systems (Sec. 3, Fig. 1) is explored level by level; every
+ * successor goes through a find-or-put on a closed-hashing table whose
+ * buckets are read by a group of cooperating threads and claimed by
+ * compare-and-swap, with a new bucket picked by the next hash-constant set
+ * when a bucket is full (Sec. 4.1, Figs. 3-4); the bucket size is
+ * configurable from 32 words down to 4 (Sec. 4.2, Fig. 5).
+ *
+ * Conventions for every entry point:
+ *   - Return value: a gx_status.  On failure gx_last_error() gives a
+ *     human-readable message (thread-local, valid until the next call on the
+ *     same thread).  No entry point aborts or traps.
+ *   - "device pointer" arguments must point to memory of the current CUDA
+ *     device; "host pointer" arguments to ordinary (or pinned) host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is issued on it; calls that return host-visible
+ *     results synchronise that stream before returning.
+ *   - Input arrays are owned by the caller and are only read during the call.
+ */
+#ifndef GX_H
+#define GX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gx_status {
+  GX_OK = 0,
+  GX_ERR_INVALID = 1,            /* bad argument or network (message says which) */
+  GX_ERR_OOM = 2,                /* workspace too small / device allocation failed */
+  GX_ERR_TABLE_FULL = 3,         /* every hash-constant set met a full bucket (Sec. 4.1) */
+  GX_ERR_FRONTIER_OVERFLOW = 4,  /* the frontier ring could not hold the next level */
+  GX_ERR_SPIN_LIMIT = 5,         /* a bounded device wait gave up */
+  GX_ERR_CUDA = 6,               /* a CUDA runtime call failed */
+  GX_ERR_STATE = 7               /* call order (e.g. stats before any exploration) */
+} gx_status;
+
+/* ------------------------------------------------------------------------------------------
+ * Networks (Sec. 3, Fig. 1).
+ *
+ * A process is an LTS: n_states local states numbered 0..n_states-1, an
+ * initial state and n_edges labelled edges (src[i] -label[i]-> dst[i]).
+ * Labels are global ids 0..n_labels-1.  A rule is a synchronisation vector:
+ * its n_parts participants (proc[j], label[j]) -- distinct processes -- move
+ * together when each has an edge with its label from its current state; every
+ * combination of such edges is one transition.  A (process, label) pair that
+ * occurs in any rule never moves alone; every other edge moves its process
+ * alone (interleaving).  result_label is kept for reference only.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct gx_lts {
+  uint32_t n_states, n_edges, initial;
+  const uint32_t *src, *label, *dst; /* host pointers, n_edges each */
+} gx_lts;
+
+typedef struct gx_rule {
+  uint32_t n_parts;
+  const uint32_t *proc, *label; /* host pointers, n_parts each */
+  uint32_t result_label;
+} gx_rule;
+
+typedef struct gx_net_desc {
+  uint32_t n_procs, n_labels;
+  const gx_lts* procs;   /* host pointer, n_procs entries */
+  uint32_t n_rules;
+  const gx_rule* rules;  /* host pointer, n_rules entries (may be NULL if 0) */
+} gx_net_desc;
+
+typedef struct gx_net gx_net; /* opaque, owned by the library; free with gx_free */
+
+/* Validate and encode a network (Sec. 3 network of LTSs; bit-packed 32-bit
+ * state vectors as in Sec. 3 and Sec. 4.2, "the vector size generally does
+ * not exceed four integers").  Each process gets ceil(log2 n_states) bits
+ * (at least 1); fields are packed LSB-first into 32-bit words whose bit 31
+ * is reserved (always set in a stored vector, so an all-zero slot is empty);
+ * a field never straddles two words.  At most 4 words (3 are padded to 4).
+ * Errors: GX_ERR_INVALID for out-of-range states/labels/processes, repeated
+ * processes in one rule, empty rules, or vectors longer than 4 words.
+ * Host-only: no device memory is touched.  *out is set only on GX_OK. */
+gx_status gx_load_network(const gx_net_desc* desc, gx_net** out);
+
+/* Release a network and everything the library holds for it.  NULL is a no-op. */
+void gx_free(gx_net* net);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gx_last_error(void);
+
+/* Vector layout chosen by gx_load_network: words per vector (1, 2 or 4 after
+ * padding) and, per process, the word index, bit offset and bit width of its
+ * field (each array n_procs long; any of them may be NULL). */
+gx_status gx_layout(const gx_net* net, uint32_t* vector_words, uint32_t* field_word,
+                    uint32_t* field_offset, uint32_t* field_bits);
+
+/* ------------------------------------------------------------------------------------------
+ * Exploration options.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct gx_explore_opts {
+  uint32_t bucket_words;   /* B, words per bucket: 4, 8, 16 or 32 (Sec. 4.2).  0 = 8 */
+  uint32_t group_lanes;    /* G, threads sharing one bucket: a power of two with
+                              1 <= G <= B / vector_words.  0 = B / vector_words
+                              (one thread per slot) */
+  uint32_t hash_rounds;    /* hash-constant sets tried per insertion, 1..64.
+                              0 = 8 (Sec. 4.1) */
+  uint32_t stop_at_first_deadlock; /* finish the level that met the first deadlock, then stop */
+  uint32_t max_levels;     /* stop after this many levels have been expanded; 0 = no limit */
+  uint32_t deadlock_cap;   /* deadlock states kept for gx_deadlocks; 0 = 1024 */
+  uint32_t ctas_per_sm;    /* persistent CTAs per SM; 0 = as many as fit */
+  uint32_t reserved0;
+  uint64_t table_bytes;    /* hash-table size; rounded down to a power-of-two number of
+                              buckets.  0 = 1 GiB */
+  uint64_t frontier_states;/* capacity of the frontier ring in vectors; rounded up to a
+                              power of two.  0 = table slots / 4 (at least 4096) */
+} gx_explore_opts;
+
+/* Fill *opts with the defaults described above. */
+gx_status gx_default_opts(gx_explore_opts* opts);
+
+/* Bytes of device workspace gx_explore needs for this network and options
+ * (table + frontier ring + control block + deadlock buffer + network tables).
+ * When opts->table_bytes is 0 the table gets 1 GiB. */
+gx_status gx_workspace_bytes(const gx_net* net, const gx_explore_opts* opts, uint64_t* bytes);
+
+/* Full breadth-first exploration from the initial state (Sec. 3; the table
+ * of Sec. 4 holds the visited set).  workspace: device pointer to at least
+ * gx_workspace_bytes() bytes, 256-byte aligned, owned by the caller and
+ * overwritten; NULL = the library allocates (cudaMallocAsync on `stream`) and
+ * frees it before returning.  On GX_OK the results are kept in `net` for
+ * gx_stats / gx_levels / gx_deadlocks.  GX_ERR_TABLE_FULL,
+ * GX_ERR_FRONTIER_OVERFLOW, GX_ERR_SPIN_LIMIT end the search (results of the
+ * levels completed so far are kept, marked incomplete).  Synchronises `stream`. */
+gx_status gx_explore(gx_net* net, const gx_explore_opts* opts, void* workspace,
+                     uint64_t workspace_bytes, void* stream);
+
+/* Deadlock search (on-the-fly deadlock checking, Sec. 1 and Sec. 3).
+ *   mode GX_DL_BFS_FIRST: breadth-first, stop after the level that met the
+ *     first deadlock (every deadlock of that level is reported);
+ *   mode GX_DL_BFS_ALL: full exploration, every deadlock reported;
+ *   mode GX_DL_GUIDED: best-first order by the scoring network set with
+ *     gx_guided_set_weights, falling back to exhaustive search; absence of
+ *     deadlocks is reported only after the whole state space was explored.
+ * out_states: host pointer receiving up to cap deadlock states, n_procs
+ * local states each (uint32); *n_found gets the total number found (may
+ * exceed cap).  Other arguments as for gx_explore. */
+enum { GX_DL_BFS_FIRST = 0, GX_DL_BFS_ALL = 1, GX_DL_GUIDED = 2 };
+gx_status gx_find_deadlocks(gx_net* net, const gx_explore_opts* opts, uint32_t mode,
+                            void* workspace, uint64_t workspace_bytes, void* stream,
+                            uint32_t* out_states, uint32_t cap, uint64_t* n_found);
+
+/* Results of the last gx_explore / gx_find_deadlocks on `net`. */
+typedef struct gx_stats_t {
+  uint64_t states;          /* distinct states found (all levels) */
+  uint64_t explored;        /* states whose successors were generated */
+  uint64_t transitions;     /* sum over explored states of their successor count,
+                               with multiplicity */
+  uint64_t n_levels;        /* BFS levels found; level 0 = {initial state} */
+  uint64_t deadlock_count;  /* explored states without successors */
+  uint64_t deadlock_sum;    /* order-free digest of the deadlock set: sum and xor of */
+  uint64_t deadlock_xor;    /* h(state) = fold_p sm64(h ^ (p << 32 | s_p)), h0 = 0 */
+  int64_t first_deadlock_level; /* -1 if none */
+  uint64_t table_slots;     /* slots in the hash table */
+  uint32_t vector_words, slot_words, bucket_words, group_lanes, hash_rounds;
+  uint32_t complete;        /* 1 = the search ended because no open state was left */
+  uint32_t status;          /* gx_status of the run */
+  uint32_t reserved;
+  double fill;              /* states / table_slots */
+  double gpu_ms;            /* device time of the search (CUDA events around it) */
+  double expand_ms;         /* summed device time of the level-expansion kernels */
+  uint64_t expand_launches; /* level-expansion kernel launches */
+  uint64_t probes;          /* buckets read by find-or-put during the search */
+  uint64_t h2d_bytes;       /* host-to-device bytes the search copied (network tables) */
+  uint64_t d2h_bytes;       /* device-to-host bytes it copied (progress, deadlock states) */
+} gx_stats_t;
+
+gx_status gx_stats(const gx_net* net, gx_stats_t* out);
+
+/* Level sizes of the last search: out[k] = number of states at BFS depth k.
+ * Writes min(cap, n_levels) entries; *n_levels gets the total. */
+gx_status gx_levels(const gx_net* net, uint64_t* out, uint32_t cap, uint32_t* n_levels);
+
+/* Deadlock states kept by the last search (at most opts.deadlock_cap), n_procs
+ * local states each, in no particular order.  *n gets the number written. */
+gx_status gx_deadlocks(const gx_net* net, uint32_t* out, uint32_t cap, uint32_t* n);
+
+/* Digest of every state in the hash table after a search: count, sum and xor
+ * of h(state) (same h as the deadlock digest).  workspace/stream must be the
+ * ones of the last search (the table is read in place). */
+gx_status gx_set_digest(gx_net* net, void* workspace, uint64_t workspace_bytes, void* stream,
+                        uint64_t* count, uint64_t* sum, uint64_t* xr);
+
+/* ------------------------------------------------------------------------------------------
+ * The isolated hash-table experiment (Sec. 5.1, Fig. "buckvsgputable"):
+ * find-or-put of n_keys keys of key_words uint32 each into a table.
+ *   keys:    device pointer, n_keys * key_words uint32, row-major; bit 31 of
+ *            every word must be clear (the table uses it as the occupied tag).
+ *   table:   device pointer, table_words uint32 (a power-of-two multiple of
+ *            bucket_words, 256-byte aligned).  Zero it first for an empty
+ *            table; it is read and written in place.
+ *   result:  device pointer, n_keys bytes, or NULL: 1 = this call inserted the
+ *            key, 0 = the key was already present, 2 = no free slot in any round.
+ *   counters: device pointer to 3 uint64 (inserted, found, failed), added to.
+ * key_words: 1, 2 or 4; bucket_words, group_lanes, hash_rounds as in
+ * gx_explore_opts (0 = default).  Asynchronous on `stream`. */
+gx_status gx_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t key_words,
+                         uint32_t bucket_words, uint32_t group_lanes, uint32_t hash_rounds,
+                         uint32_t* table, uint64_t table_words, uint8_t* result,
+                         uint64_t* counters, void* stream);
+
+/* Random-access probes used as the roofline for the table (no counterpart in
+ * the paper): over the largest power-of-two number of `bytes`-sized units that
+ * fits a device buffer of `words` uint32, `n` accesses at pseudo-random
+ * unit-aligned positions, each reading `bytes` (16, 32, 64 or 128) contiguous
+ * bytes (kind 0) or doing one 32/64/128-bit compare-and-swap (kind 1, `bytes`
+ * = 4, 8 or 16).  sink: device pointer to one uint64 that
+ * receives a checksum so the reads cannot be optimised away.  Asynchronous. */
+gx_status gx_probe_random(uint32_t kind, uint32_t* buffer, uint64_t words, uint64_t n,
+                          uint32_t bytes, uint64_t seed, uint64_t* sink, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GX_H */

@@ -1,0 +1,487 @@
+// The level loop and the C ABI of the exploration path.
+//
+// One search (Sec. 3): clear the table, insert the initial vector (level 0),
+// then per level launch one persistent expansion kernel over the open
+// vectors of that level; the host only reads a 64-byte control block between
+// levels to learn the next level's size and whether an error or a deadlock
+// occurred ("only the general progress is checked on the host side", Sec. 3).
+//
+// Workspace (one device buffer, 256-byte aligned regions):
+//   control block | network blob | deadlock buffer |
+//   frontier ring | hash table
+// The frontier is a ring of vectors indexed by absolute position: the level
+// being expanded occupies [cur_begin, cur_end) and its successors are
+// appended from cur_end on; the ring overflows when a level and its
+// successor level together exceed its capacity.  This replaces the paper's
+// scan of the hash table for open vectors (Sec. 4: the table keeps the open
+// and closed sets) -- a per-level table scan would read the whole table once
+// per level.
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gx_kernels.cuh"
+
+namespace gx {
+
+void hash_multipliers(uint64_t* out, int n) {
+  // splitmix64 stream from a fixed seed; forcing the low bit makes each odd
+  uint64_t s = 0x243F6A8885A308D3ull;  // digits of pi
+  for (int i = 0; i < n; ++i) {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    out[i] = (z ^ (z >> 31)) | 1ull;
+  }
+}
+
+}  // namespace gx
+
+namespace gxd {
+
+template <int W>
+__global__ void __launch_bounds__(gx::kBlock) digest_kernel(const gx::DigestArgs a) {
+  unsigned long long cnt = 0, sum = 0, xr = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.slots; i += stride) {
+    uint32_t v[W];
+    load_vec<W>(a.table + i * W, v);
+    bool tagged = true;
+#pragma unroll
+    for (int w = 0; w < W; ++w) tagged &= (v[w] & kTag) != 0;
+    if (!tagged) continue;
+    const uint64_t h = state_digest<W>(a.blob, a.lay, v);
+    cnt += 1;
+    sum += h;
+    xr ^= h;
+  }
+  cnt = warp_sum(cnt);
+  sum = warp_sum(sum);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) xr ^= __shfl_xor_sync(FULLMASK, xr, o);
+  if ((threadIdx.x & 31) == 0 && cnt) {
+    atomicAdd(&a.out[0], cnt);
+    atomicAdd(&a.out[1], sum);
+    atomicXor(&a.out[2], xr);
+  }
+}
+
+}  // namespace gxd
+
+namespace gx {
+
+cudaError_t launch_digest(int W, const DigestArgs& a, int grid, cudaStream_t st) {
+  if (W == 1) gxd::digest_kernel<1><<<grid, kBlock, 0, st>>>(a);
+  else if (W == 2) gxd::digest_kernel<2><<<grid, kBlock, 0, st>>>(a);
+  else gxd::digest_kernel<4><<<grid, kBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+namespace {
+
+constexpr uint64_t kAlign = 256;
+inline uint64_t align_up(uint64_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+inline uint64_t pow2_floor(uint64_t x) {
+  uint64_t p = 1;
+  while (p * 2 <= x) p *= 2;
+  return p;
+}
+inline uint64_t pow2_ceil(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p *= 2;
+  return p;
+}
+inline int ilog2(uint64_t x) {
+  int l = 0;
+  while ((1ull << l) < x) ++l;
+  return l;
+}
+
+#define GX_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return gx::fail(GX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+struct Plan {
+  int W = 0, B = 0, G = 0, rounds = 0;
+  uint32_t dl_cap = 0;
+  uint64_t nb = 0;         // buckets (power of two)
+  uint64_t fcap = 0;       // frontier ring capacity (power of two)
+  uint64_t off_ctl = 0, off_blob = 0, off_dl = 0, off_front = 0, off_table = 0;
+  uint64_t total = 0;
+  const KernelSet* ks = nullptr;
+};
+
+gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
+  gx_explore_opts d;
+  gx_default_opts(&d);
+  if (!o) o = &d;
+  P.W = (int)net.slot_words;
+  P.B = o->bucket_words ? (int)o->bucket_words : 8;
+  if (P.B != 4 && P.B != 8 && P.B != 16 && P.B != 32)
+    return fail(GX_ERR_INVALID, "bucket_words must be 4, 8, 16 or 32");
+  if (P.B < P.W)
+    return fail(GX_ERR_INVALID, "bucket_words " + std::to_string(P.B) + " is smaller than the " +
+                                    std::to_string(P.W) + "-word slots of this network");
+  const int S = P.B / P.W;
+  P.G = o->group_lanes ? (int)o->group_lanes : std::min(S, 32);
+  if (P.G < 1 || (P.G & (P.G - 1)) || P.G > S || P.G > 32)
+    return fail(GX_ERR_INVALID, "group_lanes must be a power of two between 1 and bucket_words / slot words (" +
+                                    std::to_string(S) + ")");
+  P.rounds = o->hash_rounds ? (int)o->hash_rounds : 8;
+  if (P.rounds < 1 || P.rounds > kMaxRounds) return fail(GX_ERR_INVALID, "hash_rounds must be 1..64");
+  P.ks = kernels_for(P.W, P.B, P.G);
+  if (!P.ks) return fail(GX_ERR_INVALID, "no kernel built for this (slot, bucket, group) size");
+  const uint64_t table_bytes = o->table_bytes ? o->table_bytes : (1ull << 30);
+  const uint64_t bucket_bytes = 4ull * P.B;
+  if (table_bytes < 2 * bucket_bytes) return fail(GX_ERR_INVALID, "table_bytes is smaller than two buckets");
+  P.nb = pow2_floor(table_bytes / bucket_bytes);
+  const uint64_t slots = P.nb * (uint64_t)S;
+  P.fcap = pow2_ceil(o->frontier_states ? o->frontier_states : std::max<uint64_t>(4096, slots / 4));
+  P.dl_cap = o->deadlock_cap ? o->deadlock_cap : 1024;
+  uint64_t off = 0;
+  P.off_ctl = off;
+  off = align_up(off + sizeof(Ctl));
+  P.off_blob = off;
+  off = align_up(off + 4ull * net.blob.size());
+  P.off_dl = off;
+  off = align_up(off + 4ull * P.W * P.dl_cap);
+  P.off_front = off;
+  off = align_up(off + 4ull * P.W * P.fcap);
+  P.off_table = off;
+  off = align_up(off + 4ull * P.B * P.nb);
+  P.total = off;
+  return GX_OK;
+}
+
+struct Device {
+  int sms = 0;
+  size_t smem_optin = 0;
+};
+
+gx_status device_info(Device& d) {
+  int dev = 0;
+  GX_CUDA(cudaGetDevice(&dev));
+  GX_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+  int so = 0;
+  GX_CUDA(cudaDeviceGetAttribute(&so, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  d.smem_optin = (size_t)so;
+  return GX_OK;
+}
+
+// Pinned host copy of the control block, one per thread.
+struct HostCtl {
+  Ctl* p = nullptr;
+  ~HostCtl() {
+    if (p) cudaFreeHost(p);
+  }
+};
+thread_local HostCtl g_hctl;
+
+gx_status host_ctl(Ctl*& out) {
+  if (!g_hctl.p) GX_CUDA(cudaMallocHost(reinterpret_cast<void**>(&g_hctl.p), sizeof(Ctl)));
+  out = g_hctl.p;
+  return GX_OK;
+}
+
+gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, void* ws,
+                     uint64_t ws_bytes, cudaStream_t st) {
+  const Net& net = h->net;
+  gx_explore_opts d;
+  gx_default_opts(&d);
+  const gx_explore_opts* o = opts ? opts : &d;
+  Plan P;
+  gx_status s = make_plan(net, o, P);
+  if (s != GX_OK) return s;
+  Device dev;
+  if ((s = device_info(dev)) != GX_OK) return s;
+  Ctl* hc = nullptr;
+  if ((s = host_ctl(hc)) != GX_OK) return s;
+
+  bool owned = false;
+  if (!ws) {
+    GX_CUDA(cudaMallocAsync(&ws, P.total, st));
+    owned = true;
+  } else {
+    if (ws_bytes < P.total)
+      return fail(GX_ERR_OOM, "workspace holds " + std::to_string(ws_bytes) + " bytes, need " +
+                                  std::to_string(P.total));
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(GX_ERR_INVALID, "workspace is not 256-byte aligned");
+  }
+  struct Freer {
+    void* p;
+    bool own;
+    cudaStream_t st;
+    ~Freer() {
+      if (own && p) cudaFreeAsync(p, st);
+    }
+  } freer{ws, owned, st};
+
+  char* base = static_cast<char*>(ws);
+  Ctl* ctl = reinterpret_cast<Ctl*>(base + P.off_ctl);
+  uint32_t* blob = reinterpret_cast<uint32_t*>(base + P.off_blob);
+  uint32_t* dl = reinterpret_cast<uint32_t*>(base + P.off_dl);
+  uint32_t* front = reinterpret_cast<uint32_t*>(base + P.off_front);
+  uint32_t* table = reinterpret_cast<uint32_t*>(base + P.off_table);
+
+  GX_CUDA(cudaMemcpyAsync(blob, net.blob.data(), 4 * net.blob.size(), cudaMemcpyHostToDevice, st));
+
+  cudaEvent_t ev0, ev1, ek0, ek1;
+  GX_CUDA(cudaEventCreate(&ev0));
+  GX_CUDA(cudaEventCreate(&ev1));
+  GX_CUDA(cudaEventCreate(&ek0));
+  GX_CUDA(cudaEventCreate(&ek1));
+  struct EvFree {
+    cudaEvent_t a, b, c, d;
+    ~EvFree() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      cudaEventDestroy(c);
+      cudaEventDestroy(d);
+    }
+  } evfree{ev0, ev1, ek0, ek1};
+
+  GX_CUDA(cudaEventRecord(ev0, st));
+  GX_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
+  GX_CUDA(cudaMemsetAsync(table, 0, 4ull * P.B * P.nb, st));
+
+  InitArgs ia{};
+  hash_multipliers(ia.muls.m, kMaxRounds);
+  ia.rounds = P.rounds;
+  ia.log2nb = ilog2(P.nb);
+  ia.table = table;
+  ia.frontier = front;
+  ia.ctl = ctl;
+  for (int w = 0; w < 4; ++w) ia.vec[w] = net.init_vec[w];
+  GX_CUDA(P.ks->init(ia, st));
+
+  ExpandArgs ea{};
+  ea.blob = blob;
+  ea.blob_words = (uint32_t)net.blob.size();
+  ea.lay = net.lay;
+  ea.muls = ia.muls;
+  ea.rounds = P.rounds;
+  ea.log2nb = ia.log2nb;
+  ea.table = table;
+  ea.frontier = front;
+  ea.fmask = P.fcap - 1;
+  ea.ctl = ctl;
+  ea.dl_buf = dl;
+  ea.dl_cap = P.dl_cap;
+  size_t smem = 8ull * kMaxRounds;
+  const size_t blob_bytes = 4ull * net.blob.size();
+  ea.stage = (smem + blob_bytes <= std::min<size_t>(dev.smem_optin, 96 * 1024)) ? 1 : 0;
+  if (ea.stage) smem += blob_bytes;
+  GX_CUDA(cudaFuncSetAttribute(P.ks->expand_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  GX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.ks->expand_fn, kBlock, smem));
+  if (per_sm < 1) return fail(GX_ERR_INVALID, "expansion kernel does not fit on an SM");
+  if (o->ctas_per_sm) per_sm = std::min<int>(per_sm, (int)o->ctas_per_sm);
+  const uint64_t max_grid = (uint64_t)dev.sms * per_sm;
+
+  std::vector<uint64_t> levels{1};
+  uint64_t cur_begin = 0, cur_end = 1, explored = 0;
+  int64_t first_dl = -1;
+  double expand_ms = 0;
+  uint64_t launches = 0;
+  uint32_t err = 0;
+  bool complete = false;
+  while (true) {
+    GX_CUDA(cudaMemsetAsync(&ctl->claim, 0, sizeof(unsigned long long), st));
+    ea.cur_begin = cur_begin;
+    ea.cur_end = cur_end;
+    const uint64_t warps = (cur_end - cur_begin + 31) / 32;
+    const uint64_t want = (warps + kBlock / 32 - 1) / (kBlock / 32);
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, max_grid));
+    GX_CUDA(cudaEventRecord(ek0, st));
+    GX_CUDA(P.ks->expand(ea, grid, smem, st));
+    GX_CUDA(cudaEventRecord(ek1, st));
+    GX_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    GX_CUDA(cudaStreamSynchronize(st));
+    float ms = 0;
+    GX_CUDA(cudaEventElapsedTime(&ms, ek0, ek1));
+    expand_ms += ms;
+    ++launches;
+    explored += cur_end - cur_begin;
+    if (first_dl < 0 && hc->dl_count > 0) first_dl = (int64_t)levels.size() - 1;
+    err = hc->error;
+    const uint64_t next_end = hc->next_end;
+    if (next_end > cur_end) levels.push_back(next_end - cur_end);
+    if (err) break;
+    if (next_end == cur_end) {
+      complete = true;
+      break;
+    }
+    cur_begin = cur_end;
+    cur_end = next_end;
+    if (stop_first && hc->dl_count > 0) break;
+    if (o->max_levels && launches >= o->max_levels) break;
+  }
+  GX_CUDA(cudaEventRecord(ev1, st));
+  GX_CUDA(cudaStreamSynchronize(st));
+  float total_ms = 0;
+  GX_CUDA(cudaEventElapsedTime(&total_ms, ev0, ev1));
+
+  // deadlock states
+  const uint64_t ndl = std::min<uint64_t>(hc->dl_count, P.dl_cap);
+  std::vector<uint32_t> dlw(ndl * P.W);
+  if (ndl) {
+    GX_CUDA(cudaMemcpyAsync(dlw.data(), dl, 4 * dlw.size(), cudaMemcpyDeviceToHost, st));
+    GX_CUDA(cudaStreamSynchronize(st));
+  }
+  h->deadlocks.assign(ndl * net.n_procs, 0);
+  for (uint64_t i = 0; i < ndl; ++i) {
+    uint32_t w4[4] = {0, 0, 0, 0};
+    for (int w = 0; w < P.W; ++w) w4[w] = dlw[i * P.W + w];
+    unpack_host(net, w4, h->deadlocks.data() + i * net.n_procs);
+  }
+
+  gx_stats_t& S = h->stats;
+  std::memset(&S, 0, sizeof(S));
+  S.states = hc->next_end;
+  S.explored = explored;
+  S.transitions = hc->transitions;
+  S.n_levels = levels.size();
+  S.deadlock_count = hc->dl_count;
+  S.deadlock_sum = hc->dl_sum;
+  S.deadlock_xor = hc->dl_xor;
+  S.first_deadlock_level = first_dl;
+  S.table_slots = P.nb * (uint64_t)(P.B / P.W);
+  S.vector_words = net.vector_words;
+  S.slot_words = (uint32_t)P.W;
+  S.bucket_words = (uint32_t)P.B;
+  S.group_lanes = (uint32_t)P.G;
+  S.hash_rounds = (uint32_t)P.rounds;
+  S.complete = complete ? 1 : 0;
+  S.fill = (double)S.states / (double)S.table_slots;
+  S.gpu_ms = total_ms;
+  S.expand_ms = expand_ms;
+  S.expand_launches = launches;
+  S.probes = hc->probes;
+  S.h2d_bytes = 4ull * net.blob.size();
+  S.d2h_bytes = sizeof(Ctl) * launches + 4ull * dlw.size();
+  h->levels = levels;
+  h->ws_off_ctl = P.off_ctl;
+  h->ws_off_blob = P.off_blob;
+  h->ws_off_table = P.off_table;
+  h->ws_total = P.total;
+  h->have_result = true;
+  gx_status rs = GX_OK;
+  if (err & ERR_TABLE_FULL) rs = fail(GX_ERR_TABLE_FULL, "hash table full: no free slot under any hash-constant set");
+  else if (err & ERR_FRONTIER) rs = fail(GX_ERR_FRONTIER_OVERFLOW, "frontier ring overflow; raise frontier_states");
+  else if (err & ERR_SPIN) rs = fail(GX_ERR_SPIN_LIMIT, "a device wait hit its iteration limit");
+  S.status = (uint32_t)rs;
+  return rs;
+}
+
+}  // namespace
+}  // namespace gx
+
+extern "C" {
+
+gx_status gx_workspace_bytes(const gx_net* h, const gx_explore_opts* opts, uint64_t* bytes) {
+  gx::clear_error();
+  if (!h || !bytes) return gx::fail(GX_ERR_INVALID, "net or bytes is NULL");
+  gx::Plan P;
+  gx_status s = gx::make_plan(h->net, opts, P);
+  if (s != GX_OK) return s;
+  *bytes = P.total;
+  return GX_OK;
+}
+
+gx_status gx_explore(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t ws_bytes, void* stream) {
+  gx::clear_error();
+  if (!h) return gx::fail(GX_ERR_INVALID, "net is NULL");
+  return gx::run_search(h, opts, opts && opts->stop_at_first_deadlock, ws, ws_bytes,
+                        static_cast<cudaStream_t>(stream));
+}
+
+gx_status gx_find_deadlocks(gx_net* h, const gx_explore_opts* opts, uint32_t mode, void* ws,
+                            uint64_t ws_bytes, void* stream, uint32_t* out_states, uint32_t cap,
+                            uint64_t* n_found) {
+  gx::clear_error();
+  if (!h) return gx::fail(GX_ERR_INVALID, "net is NULL");
+  if (cap && !out_states) return gx::fail(GX_ERR_INVALID, "out_states is NULL");
+  gx_status s;
+  if (mode == GX_DL_BFS_FIRST || mode == GX_DL_BFS_ALL) {
+    s = gx::run_search(h, opts, mode == GX_DL_BFS_FIRST, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+  } else if (mode == GX_DL_GUIDED) {
+    return gx::fail(GX_ERR_INVALID, "guided mode needs scoring weights (not set)");
+  } else {
+    return gx::fail(GX_ERR_INVALID, "unknown deadlock-search mode");
+  }
+  if (!h->have_result) return s;
+  const uint32_t n = h->net.n_procs;
+  const uint64_t have = h->deadlocks.size() / n;
+  const uint64_t k = std::min<uint64_t>(have, cap);
+  if (k) std::memcpy(out_states, h->deadlocks.data(), 4ull * n * k);
+  if (n_found) *n_found = h->stats.deadlock_count;
+  return s;
+}
+
+gx_status gx_stats(const gx_net* h, gx_stats_t* out) {
+  gx::clear_error();
+  if (!h || !out) return gx::fail(GX_ERR_INVALID, "net or out is NULL");
+  if (!h->have_result) return gx::fail(GX_ERR_STATE, "no search has run on this network");
+  *out = h->stats;
+  return GX_OK;
+}
+
+gx_status gx_levels(const gx_net* h, uint64_t* out, uint32_t cap, uint32_t* n_levels) {
+  gx::clear_error();
+  if (!h) return gx::fail(GX_ERR_INVALID, "net is NULL");
+  if (!h->have_result) return gx::fail(GX_ERR_STATE, "no search has run on this network");
+  if (cap && !out) return gx::fail(GX_ERR_INVALID, "out is NULL");
+  for (size_t i = 0; i < h->levels.size() && i < cap; ++i) out[i] = h->levels[i];
+  if (n_levels) *n_levels = (uint32_t)h->levels.size();
+  return GX_OK;
+}
+
+gx_status gx_deadlocks(const gx_net* h, uint32_t* out, uint32_t cap, uint32_t* n) {
+  gx::clear_error();
+  if (!h) return gx::fail(GX_ERR_INVALID, "net is NULL");
+  if (!h->have_result) return gx::fail(GX_ERR_STATE, "no search has run on this network");
+  if (cap && !out) return gx::fail(GX_ERR_INVALID, "out is NULL");
+  const uint32_t np = h->net.n_procs;
+  const uint64_t have = h->deadlocks.size() / np;
+  const uint64_t k = std::min<uint64_t>(have, cap);
+  if (k) std::memcpy(out, h->deadlocks.data(), 4ull * np * k);
+  if (n) *n = (uint32_t)k;
+  return GX_OK;
+}
+
+gx_status gx_set_digest(gx_net* h, void* ws, uint64_t ws_bytes, void* stream, uint64_t* count,
+                        uint64_t* sum, uint64_t* xr) {
+  gx::clear_error();
+  if (!h || !ws) return gx::fail(GX_ERR_INVALID, "net or workspace is NULL");
+  if (!h->have_result) return gx::fail(GX_ERR_STATE, "no search has run on this network");
+  if (ws_bytes && ws_bytes < h->ws_total) return gx::fail(GX_ERR_INVALID, "workspace smaller than the last search's");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  gx::Device dev;
+  gx_status s = gx::device_info(dev);
+  if (s != GX_OK) return s;
+  char* base = static_cast<char*>(ws);
+  unsigned long long* out = reinterpret_cast<gx::Ctl*>(base + h->ws_off_ctl)->digest;
+  GX_CUDA(cudaMemsetAsync(out, 0, 3 * sizeof(unsigned long long), st));
+  gx::DigestArgs a{};
+  a.table = reinterpret_cast<const uint32_t*>(base + h->ws_off_table);
+  a.slots = h->stats.table_slots;
+  a.blob = reinterpret_cast<const uint32_t*>(base + h->ws_off_blob);
+  a.lay = h->net.lay;
+  a.out = out;
+  GX_CUDA(gx::launch_digest((int)h->stats.slot_words, a, dev.sms * 8, st));
+  unsigned long long r[3];
+  GX_CUDA(cudaMemcpyAsync(r, out, sizeof(r), cudaMemcpyDeviceToHost, st));
+  GX_CUDA(cudaStreamSynchronize(st));
+  if (count) *count = r[0];
+  if (sum) *sum = r[1];
+  if (xr) *xr = r[2];
+  return GX_OK;
+}
+
+}  // extern "C"

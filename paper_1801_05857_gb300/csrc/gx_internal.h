@@ -1,0 +1,67 @@
+// Internal host-side definitions shared by the gx translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gx.h"
+
+namespace gx {
+
+// Error reporting: every entry point records a message and returns a status.
+gx_status fail(gx_status st, const std::string& msg);
+void clear_error();
+
+// Words of one packed vector are tagged in bit 31 (always set in a stored
+// vector) so that an all-zero slot means "empty"; payload uses bits 0..30.
+constexpr uint32_t kTag = 0x80000000u;
+constexpr uint32_t kPayloadBits = 31;
+constexpr uint32_t kMaxWords = 4;
+
+// Encoded network tables, one uint32 blob uploaded to the device and staged
+// into shared memory by the kernels.  Offsets (in words) of each array:
+struct NetBlobLayout {
+  uint32_t n_procs, n_classes, n_rules;
+  uint32_t proc_word;   // [n_procs]  word index of each process field
+  uint32_t proc_shift;  // [n_procs]  bit offset
+  uint32_t proc_mask;   // [n_procs]  (1 << bits) - 1
+  uint32_t cls_proc;    // [n_classes] process of each edge class
+  uint32_t cls_base;    // [n_classes] start of the class's offset array in `coff`
+  uint32_t coff;        // per class: n_states(proc) + 1 offsets into `cdelta`
+  uint32_t cdelta;      // xor deltas (s ^ t) << shift, one per edge of the class
+  uint32_t rule_off;    // [n_rules + 1] into rule_cls
+  uint32_t rule_cls;    // class id of each rule participant
+  uint32_t total;       // blob length in words
+};
+
+struct Net {
+  uint32_t n_procs = 0, n_labels = 0;
+  uint32_t vector_words = 0;  // L after packing (1..4)
+  uint32_t slot_words = 0;    // W: L, with 3 padded to 4
+  std::vector<uint32_t> n_states, initial;
+  std::vector<uint32_t> field_word, field_shift, field_bits;
+  uint32_t max_rule_parts = 0;
+  std::vector<uint32_t> blob;
+  NetBlobLayout lay{};
+  uint32_t init_vec[kMaxWords] = {0, 0, 0, 0};
+};
+
+}  // namespace gx
+
+// The opaque handle: the encoded network plus the results of the last search.
+struct gx_net {
+  gx::Net net;
+  bool have_result = false;
+  gx_stats_t stats{};
+  std::vector<uint64_t> levels;
+  std::vector<uint32_t> deadlocks;  // unpacked, n_procs per state
+  // workspace regions of the last search (for gx_set_digest)
+  uint64_t ws_off_ctl = 0, ws_off_blob = 0, ws_off_table = 0, ws_total = 0;
+};
+
+namespace gx {
+// Host-side codec (used for the initial vector and to unpack reported states).
+void pack_host(const Net& net, const uint32_t* local, uint32_t* words);
+void unpack_host(const Net& net, const uint32_t* words, uint32_t* local);
+}  // namespace gx

@@ -1,0 +1,104 @@
+// Host-visible interface between the level loop and the templated kernels.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "gx_internal.h"
+
+namespace gx {
+
+constexpr int kMaxRounds = 64;
+constexpr int kBlock = 256;  // threads per CTA for every exploration kernel
+
+enum : uint32_t { ERR_TABLE_FULL = 1u, ERR_FRONTIER = 2u, ERR_SPIN = 4u };
+
+// Device control block of one search (lives at the start of the workspace).
+struct Ctl {
+  unsigned long long claim;        // frontier chunks handed out in the current level
+  unsigned long long next_end;     // absolute end of the frontier ring's filled part
+  unsigned long long transitions;  // successors generated, with multiplicity
+  unsigned long long dl_count, dl_sum, dl_xor;
+  unsigned long long probes;       // buckets read by find-or-put
+  unsigned int error;              // ERR_* bits
+  unsigned int pad;
+  unsigned long long digest[3];    // gx_set_digest: count, sum, xor
+};
+static_assert(sizeof(Ctl) <= 256, "control block");
+
+// Hash-constant multipliers travel by value in the kernel parameters.
+struct Muls {
+  uint64_t m[kMaxRounds];
+};
+
+struct ExpandArgs {
+  const uint32_t* blob;      // encoded network (global memory)
+  uint32_t blob_words;
+  int stage;                 // 1: copy the blob into shared memory first
+  NetBlobLayout lay;
+  Muls muls;                 // hash-constant multipliers
+  int rounds;
+  int log2nb;                // table has 2^log2nb buckets
+  uint32_t* table;
+  uint32_t* frontier;        // ring of vectors, W words each
+  uint64_t fmask;            // ring capacity - 1 (capacity is a power of two)
+  uint64_t cur_begin, cur_end;  // absolute indices of the level being expanded
+  Ctl* ctl;
+  uint32_t* dl_buf;          // deadlock vectors, W words each
+  uint32_t dl_cap;
+};
+
+struct InitArgs {
+  Muls muls;
+  int rounds, log2nb;
+  uint32_t* table;
+  uint32_t* frontier;
+  Ctl* ctl;
+  uint32_t vec[4];
+};
+
+struct DigestArgs {
+  const uint32_t* table;
+  uint64_t slots;
+  const uint32_t* blob;
+  NetBlobLayout lay;
+  unsigned long long* out;   // count, sum, xor
+};
+
+struct FopArgs {
+  const uint32_t* keys;
+  uint64_t n;
+  uint32_t* table;
+  int log2nb, rounds;
+  Muls muls;
+  uint8_t* result;
+  unsigned long long* counters;  // inserted, found, failed
+};
+
+struct KernelSet {
+  cudaError_t (*expand)(const ExpandArgs&, int grid, size_t smem, cudaStream_t);
+  cudaError_t (*init)(const InitArgs&, cudaStream_t);
+  cudaError_t (*fop)(const FopArgs&, int grid, cudaStream_t);
+  const void* expand_fn;  // for occupancy queries and attributes
+  const void* fop_fn;
+};
+
+// Kernels for slot width W, bucket words B and group lanes G; nullptr if the
+// combination is not built.
+const KernelSet* kernels_w1(int B, int G);
+const KernelSet* kernels_w2(int B, int G);
+const KernelSet* kernels_w4(int B, int G);
+inline const KernelSet* kernels_for(int W, int B, int G) {
+  if (W == 1) return kernels_w1(B, G);
+  if (W == 2) return kernels_w2(B, G);
+  if (W == 4) return kernels_w4(B, G);
+  return nullptr;
+}
+
+cudaError_t launch_digest(int W, const DigestArgs& a, int grid, cudaStream_t st);
+
+// Hash-constant multipliers: odd 64-bit values drawn from splitmix64.
+void hash_multipliers(uint64_t* out, int n);
+
+}  // namespace gx

@@ -1,0 +1,162 @@
+// C ABI of the isolated hash-table experiment (Sec. 5.1) and of the
+// random-access probes that give the table its roofline.
+
+#include <string>
+
+#include "gx_kernels.cuh"
+
+namespace gxd {
+
+// Counter-based position stream: access i of a probe run goes to unit
+// mix64(seed + i) & (n_units - 1) (n_units a power of two), so every access is
+// independent.  Each thread keeps kInFlight accesses in flight.
+constexpr int kInFlight = 4;
+
+__global__ void __launch_bounds__(gx::kBlock)
+probe_gather_kernel(const uint32_t* __restrict__ buf, uint64_t unit_mask, int unit_words, uint64_t n,
+                    uint64_t seed, unsigned long long* sink) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kInFlight;
+  uint32_t acc = 0;
+  for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kInFlight; i0 < n; i0 += stride) {
+    uint4 x[kInFlight][2];
+#pragma unroll
+    for (int j = 0; j < kInFlight; ++j) {
+      const uint64_t u = mix64(seed + i0 + j) & unit_mask;
+      const uint4* p = reinterpret_cast<const uint4*>(buf + u * unit_words);
+      x[j][0] = (i0 + j < n) ? __ldcg(p) : make_uint4(0, 0, 0, 0);
+      x[j][1] = (i0 + j < n && unit_words >= 8) ? __ldcg(p + 1) : make_uint4(0, 0, 0, 0);
+      for (int k = 2; k < unit_words / 4; ++k) {
+        const uint4 y = (i0 + j < n) ? __ldcg(p + k) : make_uint4(0, 0, 0, 0);
+        acc ^= y.x ^ y.w;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kInFlight; ++j) acc ^= x[j][0].x ^ x[j][0].w ^ x[j][1].y ^ x[j][1].z;
+  }
+  acc = __reduce_xor_sync(FULLMASK, acc);
+  if ((threadIdx.x & 31) == 0 && acc) atomicXor(sink, (unsigned long long)acc);
+}
+
+__global__ void __launch_bounds__(gx::kBlock)
+probe_cas_kernel(uint32_t* __restrict__ buf, uint64_t unit_mask, int unit_words, uint64_t n,
+                 uint64_t seed, unsigned long long* sink) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t acc = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t u = mix64(seed + i) & unit_mask;
+    uint32_t* p = buf + u * unit_words;
+    const uint32_t tag = (uint32_t)(i | 1u) | kTag;
+    if (unit_words == 1) {
+      uint32_t v[1] = {tag}, o[1];
+      cas_slot<1>(p, v, o);
+      acc ^= o[0];
+    } else if (unit_words == 2) {
+      uint32_t v[2] = {tag, tag}, o[2];
+      cas_slot<2>(p, v, o);
+      acc ^= o[0] ^ o[1];
+    } else {
+      uint32_t v[4] = {tag, tag, tag, tag}, o[4];
+      cas_slot<4>(p, v, o);
+      acc ^= o[0] ^ o[3];
+    }
+  }
+  acc = __reduce_xor_sync(FULLMASK, acc);
+  if ((threadIdx.x & 31) == 0 && acc) atomicXor(sink, (unsigned long long)acc);
+}
+
+}  // namespace gxd
+
+namespace {
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+}  // namespace
+
+extern "C" {
+
+gx_status gx_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t key_words,
+                         uint32_t bucket_words, uint32_t group_lanes, uint32_t hash_rounds,
+                         uint32_t* table, uint64_t table_words, uint8_t* result,
+                         uint64_t* counters, void* stream) {
+  gx::clear_error();
+  if (key_words != 1 && key_words != 2 && key_words != 4)
+    return gx::fail(GX_ERR_INVALID, "key_words must be 1, 2 or 4");
+  const int W = (int)key_words;
+  const int B = bucket_words ? (int)bucket_words : 8;
+  if (B != 4 && B != 8 && B != 16 && B != 32) return gx::fail(GX_ERR_INVALID, "bucket_words must be 4, 8, 16 or 32");
+  if (B < W) return gx::fail(GX_ERR_INVALID, "bucket smaller than one key");
+  const int S = B / W;
+  const int G = group_lanes ? (int)group_lanes : (S < 32 ? S : 32);
+  const int rounds = hash_rounds ? (int)hash_rounds : 8;
+  if (rounds < 1 || rounds > gx::kMaxRounds) return gx::fail(GX_ERR_INVALID, "hash_rounds must be 1..64");
+  const gx::KernelSet* ks = gx::kernels_for(W, B, G);
+  if (!ks) return gx::fail(GX_ERR_INVALID, "group_lanes must be a power of two dividing bucket_words / key_words");
+  if (!table || !counters || (n_keys && !keys)) return gx::fail(GX_ERR_INVALID, "NULL device pointer");
+  if (reinterpret_cast<uintptr_t>(table) % 256) return gx::fail(GX_ERR_INVALID, "table is not 256-byte aligned");
+  if (table_words % B) return gx::fail(GX_ERR_INVALID, "table_words is not a multiple of bucket_words");
+  const uint64_t nb = table_words / B;
+  if (nb < 2 || (nb & (nb - 1))) return gx::fail(GX_ERR_INVALID, "bucket count must be a power of two >= 2");
+  if (n_keys == 0) return GX_OK;
+  int log2nb = 0;
+  while ((1ull << log2nb) < nb) ++log2nb;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  gx::FopArgs a{};
+  a.keys = keys;
+  a.n = n_keys;
+  a.table = table;
+  a.log2nb = log2nb;
+  a.rounds = rounds;
+  gx::hash_multipliers(a.muls.m, gx::kMaxRounds);
+  a.result = result;
+  a.counters = reinterpret_cast<unsigned long long*>(counters);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks->fop_fn, gx::kBlock, 0);
+  if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
+  const uint64_t groups_needed = n_keys;
+  const uint64_t blocks_needed = (groups_needed * G + gx::kBlock - 1) / gx::kBlock;
+  const uint64_t cap = (uint64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+  const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
+  e = ks->fop(a, grid > 0 ? grid : 1, st);
+  if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
+  return GX_OK;
+}
+
+gx_status gx_probe_random(uint32_t kind, uint32_t* buffer, uint64_t words, uint64_t n,
+                          uint32_t bytes, uint64_t seed, uint64_t* sink, void* stream) {
+  gx::clear_error();
+  if (!buffer || !sink) return gx::fail(GX_ERR_INVALID, "NULL device pointer");
+  if (reinterpret_cast<uintptr_t>(buffer) % 256) return gx::fail(GX_ERR_INVALID, "buffer is not 256-byte aligned");
+  int unit_words;
+  if (kind == 0) {
+    if (bytes != 16 && bytes != 32 && bytes != 64 && bytes != 128)
+      return gx::fail(GX_ERR_INVALID, "gather bytes must be 16, 32, 64 or 128");
+    unit_words = (int)bytes / 4;
+  } else if (kind == 1) {
+    if (bytes != 4 && bytes != 8 && bytes != 16) return gx::fail(GX_ERR_INVALID, "CAS bytes must be 4, 8 or 16");
+    unit_words = (int)bytes / 4;
+  } else {
+    return gx::fail(GX_ERR_INVALID, "kind must be 0 (gather) or 1 (CAS)");
+  }
+  uint64_t n_units = 1;
+  while (n_units * 2 * unit_words <= words) n_units *= 2;  // largest power of two that fits
+  if ((uint64_t)unit_words > words) return gx::fail(GX_ERR_INVALID, "buffer smaller than one access");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int grid = sm_count() * 8;
+  if (kind == 0)
+    gxd::probe_gather_kernel<<<grid, gx::kBlock, 0, st>>>(buffer, n_units - 1, unit_words, n, seed,
+                                                          reinterpret_cast<unsigned long long*>(sink));
+  else
+    gxd::probe_cas_kernel<<<grid, gx::kBlock, 0, st>>>(buffer, n_units - 1, unit_words, n, seed,
+                                                       reinterpret_cast<unsigned long long*>(sink));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
+  return GX_OK;
+}
+
+}  // extern "C"

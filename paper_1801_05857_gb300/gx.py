@@ -1,0 +1,288 @@
+"""Thin ctypes binding of the gx C ABI (include/gx.h).
+
+Every function marshals arguments and calls the entry point of the same name;
+all exploration work runs in the CUDA library.  PyTorch only provides device
+memory (workspaces, key and table buffers) and the current CUDA stream.  If
+libgx.so is missing, import of this module still succeeds but every call
+raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+P = ctypes.POINTER
+u32, u64, i64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64
+
+GX_OK, GX_ERR_INVALID, GX_ERR_OOM, GX_ERR_TABLE_FULL = 0, 1, 2, 3
+GX_ERR_FRONTIER_OVERFLOW, GX_ERR_SPIN_LIMIT, GX_ERR_CUDA, GX_ERR_STATE = 4, 5, 6, 7
+GX_DL_BFS_FIRST, GX_DL_BFS_ALL, GX_DL_GUIDED = 0, 1, 2
+STATUS_NAMES = {0: "GX_OK", 1: "GX_ERR_INVALID", 2: "GX_ERR_OOM", 3: "GX_ERR_TABLE_FULL",
+                4: "GX_ERR_FRONTIER_OVERFLOW", 5: "GX_ERR_SPIN_LIMIT", 6: "GX_ERR_CUDA",
+                7: "GX_ERR_STATE"}
+
+
+class GxError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class gx_lts(ctypes.Structure):
+    _fields_ = [("n_states", u32), ("n_edges", u32), ("initial", u32),
+                ("src", P(u32)), ("label", P(u32)), ("dst", P(u32))]
+
+
+class gx_rule(ctypes.Structure):
+    _fields_ = [("n_parts", u32), ("proc", P(u32)), ("label", P(u32)), ("result_label", u32)]
+
+
+class gx_net_desc(ctypes.Structure):
+    _fields_ = [("n_procs", u32), ("n_labels", u32), ("procs", P(gx_lts)),
+                ("n_rules", u32), ("rules", P(gx_rule))]
+
+
+class gx_explore_opts(ctypes.Structure):
+    _fields_ = [("bucket_words", u32), ("group_lanes", u32), ("hash_rounds", u32),
+                ("stop_at_first_deadlock", u32), ("max_levels", u32), ("deadlock_cap", u32),
+                ("ctas_per_sm", u32), ("reserved0", u32), ("table_bytes", u64),
+                ("frontier_states", u64)]
+
+
+class gx_stats_t(ctypes.Structure):
+    _fields_ = [("states", u64), ("explored", u64), ("transitions", u64), ("n_levels", u64),
+                ("deadlock_count", u64), ("deadlock_sum", u64), ("deadlock_xor", u64),
+                ("first_deadlock_level", i64), ("table_slots", u64),
+                ("vector_words", u32), ("slot_words", u32), ("bucket_words", u32),
+                ("group_lanes", u32), ("hash_rounds", u32), ("complete", u32), ("status", u32),
+                ("reserved", u32), ("fill", ctypes.c_double), ("gpu_ms", ctypes.c_double),
+                ("expand_ms", ctypes.c_double), ("expand_launches", u64), ("probes", u64),
+                ("h2d_bytes", u64), ("d2h_bytes", u64)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libgx.so (building it first if asked and the toolkit is present)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise GxError(GX_ERR_INVALID, f"CUDA library {path} is not built; run "
+                      "python -m paper_1801_05857_gb300.build")
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    sig = {
+        "gx_load_network": ([P(gx_net_desc), P(vp)], ctypes.c_int),
+        "gx_free": ([vp], None),
+        "gx_last_error": ([], ctypes.c_char_p),
+        "gx_layout": ([vp, P(u32), P(u32), P(u32), P(u32)], ctypes.c_int),
+        "gx_default_opts": ([P(gx_explore_opts)], ctypes.c_int),
+        "gx_workspace_bytes": ([vp, P(gx_explore_opts), P(u64)], ctypes.c_int),
+        "gx_explore": ([vp, P(gx_explore_opts), vp, u64, vp], ctypes.c_int),
+        "gx_find_deadlocks": ([vp, P(gx_explore_opts), u32, vp, u64, vp, P(u32), u32, P(u64)],
+                              ctypes.c_int),
+        "gx_stats": ([vp, P(gx_stats_t)], ctypes.c_int),
+        "gx_levels": ([vp, P(u64), u32, P(u32)], ctypes.c_int),
+        "gx_deadlocks": ([vp, P(u32), u32, P(u32)], ctypes.c_int),
+        "gx_set_digest": ([vp, vp, u64, vp, P(u64), P(u64), P(u64)], ctypes.c_int),
+        "gx_find_or_put": ([vp, u64, u32, u32, u32, u32, vp, u64, vp, vp, vp], ctypes.c_int),
+        "gx_probe_random": ([u32, vp, u64, u64, u32, u64, vp, vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def header_symbols() -> list:
+    """Entry points declared in include/gx.h."""
+    hdr = os.path.join(_build.INCLUDE, "gx.h")
+    txt = open(hdr).read()
+    return sorted(set(re.findall(r"^\s*(?:gx_status|void|const char\*)\s+(gx_\w+)\s*\(", txt, re.M)))
+
+
+def _check(st: int):
+    if st != GX_OK:
+        raise GxError(st, lib().gx_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# --------------------------------------------------------------------------------------------
+# networks
+# --------------------------------------------------------------------------------------------
+
+class Net:
+    """Owner of a gx_net handle (gx_free on deletion)."""
+
+    def __init__(self, handle: int, n_procs: int):
+        self.handle = handle
+        self.n_procs = n_procs
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.gx_free(self.handle)
+            self.handle = None
+
+
+def load_network(net) -> Net:
+    """gx_load_network from an inputs.Network (or its flat() dict)."""
+    f = net.flat() if hasattr(net, "flat") else net
+    n = int(f["n_procs"])
+    edges = np.ascontiguousarray(f["edges"], dtype=np.uint32).reshape(-1, 3)
+    keep = []
+    procs = (gx_lts * n)()
+    for p in range(n):
+        e0, e1 = int(f["edge_off"][p]), int(f["edge_off"][p + 1])
+        cols = [np.ascontiguousarray(edges[e0:e1, k]) for k in range(3)]
+        keep.extend(cols)
+        procs[p].n_states = int(f["n_states"][p])
+        procs[p].n_edges = e1 - e0
+        procs[p].initial = int(f["initial"][p])
+        procs[p].src, procs[p].label, procs[p].dst = [c.ctypes.data_as(P(u32)) for c in cols]
+    n_rules = len(f["rule_off"]) - 1
+    rules = (gx_rule * max(n_rules, 1))()
+    parts = np.ascontiguousarray(f["rule_parts"], dtype=np.uint32).reshape(-1, 2)
+    for r in range(n_rules):
+        j0, j1 = int(f["rule_off"][r]), int(f["rule_off"][r + 1])
+        pc = np.ascontiguousarray(parts[j0:j1, 0])
+        lc = np.ascontiguousarray(parts[j0:j1, 1])
+        keep.extend([pc, lc])
+        rules[r].n_parts = j1 - j0
+        rules[r].proc = pc.ctypes.data_as(P(u32))
+        rules[r].label = lc.ctypes.data_as(P(u32))
+        rules[r].result_label = int(f["rule_result"][r]) if len(f["rule_result"]) else 0
+    desc = gx_net_desc(n, int(f["n_labels"]), procs, n_rules, rules)
+    h = ctypes.c_void_p()
+    _check(lib().gx_load_network(ctypes.byref(desc), ctypes.byref(h)))
+    return Net(h.value, n)
+
+
+def layout(net: Net) -> dict:
+    w = u32()
+    n = net.n_procs
+    fw, fo, fb = (np.zeros(n, dtype=np.uint32) for _ in range(3))
+    _check(lib().gx_layout(net.handle, ctypes.byref(w), fw.ctypes.data_as(P(u32)),
+                           fo.ctypes.data_as(P(u32)), fb.ctypes.data_as(P(u32))))
+    return dict(vector_words=int(w.value), field_word=fw, field_offset=fo, field_bits=fb)
+
+
+def default_opts(**kw) -> gx_explore_opts:
+    o = gx_explore_opts()
+    _check(lib().gx_default_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, int(v))
+    return o
+
+
+def workspace_bytes(net: Net, opts: gx_explore_opts | None = None) -> int:
+    n = u64()
+    _check(lib().gx_workspace_bytes(net.handle, ctypes.byref(opts) if opts else None, ctypes.byref(n)))
+    return int(n.value)
+
+
+def alloc_workspace(net: Net, opts: gx_explore_opts | None = None, device="cuda"):
+    """A torch uint8 device buffer of gx_workspace_bytes() bytes."""
+    import torch
+    return torch.empty(workspace_bytes(net, opts), dtype=torch.uint8, device=device)
+
+
+def explore(net: Net, opts: gx_explore_opts | None = None, workspace=None, stream=None) -> int:
+    """gx_explore; returns the status (GX_OK) or raises GxError."""
+    nbytes = workspace.numel() if workspace is not None else 0
+    _check(lib().gx_explore(net.handle, ctypes.byref(opts) if opts else None, _ptr(workspace),
+                            nbytes, _stream(stream)))
+    return GX_OK
+
+
+def find_deadlocks(net: Net, mode: int, opts: gx_explore_opts | None = None, workspace=None,
+                   stream=None, cap: int = 1024):
+    """gx_find_deadlocks; returns (n_found, (k, n_procs) array of reported states)."""
+    out = np.zeros((max(cap, 1), net.n_procs), dtype=np.uint32)
+    nf = u64()
+    nbytes = workspace.numel() if workspace is not None else 0
+    _check(lib().gx_find_deadlocks(net.handle, ctypes.byref(opts) if opts else None, mode,
+                                   _ptr(workspace), nbytes, _stream(stream),
+                                   out.ctypes.data_as(P(u32)), cap, ctypes.byref(nf)))
+    k = min(int(nf.value), cap)
+    return int(nf.value), out[:k].copy()
+
+
+def stats(net: Net) -> dict:
+    s = gx_stats_t()
+    _check(lib().gx_stats(net.handle, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in gx_stats_t._fields_ if name != "reserved"}
+
+
+def levels(net: Net) -> list:
+    n = u32()
+    _check(lib().gx_levels(net.handle, None, 0, ctypes.byref(n)))
+    out = np.zeros(max(int(n.value), 1), dtype=np.uint64)
+    _check(lib().gx_levels(net.handle, out.ctypes.data_as(P(u64)), int(n.value), ctypes.byref(n)))
+    return [int(x) for x in out[:int(n.value)]]
+
+
+def deadlocks(net: Net, cap: int = 1 << 20) -> np.ndarray:
+    out = np.zeros((cap, net.n_procs), dtype=np.uint32)
+    n = u32()
+    _check(lib().gx_deadlocks(net.handle, out.ctypes.data_as(P(u32)), cap, ctypes.byref(n)))
+    return out[:int(n.value)].copy()
+
+
+def set_digest(net: Net, workspace, stream=None):
+    c, s, x = u64(), u64(), u64()
+    _check(lib().gx_set_digest(net.handle, _ptr(workspace), workspace.numel(), _stream(stream),
+                               ctypes.byref(c), ctypes.byref(s), ctypes.byref(x)))
+    return int(c.value), int(s.value), int(x.value)
+
+
+# --------------------------------------------------------------------------------------------
+# isolated table experiment and probes
+# --------------------------------------------------------------------------------------------
+
+def find_or_put(keys, key_words: int, table, counters, result=None, bucket_words: int = 8,
+                group_lanes: int = 0, hash_rounds: int = 0, stream=None) -> None:
+    """gx_find_or_put on torch device tensors (keys: uint32/int32 with n*key_words
+    elements; table: 32-bit, zeroed by the caller; counters: 3 x 64-bit)."""
+    n = keys.numel() // key_words
+    _check(lib().gx_find_or_put(_ptr(keys), n, key_words, bucket_words, group_lanes, hash_rounds,
+                                _ptr(table), table.numel(), _ptr(result), _ptr(counters),
+                                _stream(stream)))
+
+
+def probe_random(kind: int, buffer, n: int, nbytes: int, seed: int, sink, stream=None) -> None:
+    _check(lib().gx_probe_random(kind, _ptr(buffer), buffer.numel(), n, nbytes, seed, _ptr(sink),
+                                 _stream(stream)))

@@ -240,6 +240,27 @@ def no_sync_network(seed: int, n_procs: int, n_states: int, deg_lo: int = 0, deg
 
 
 # --------------------------------------------------------------------------------------------
+# Named workloads (generator arguments)
+# --------------------------------------------------------------------------------------------
+
+WORKLOADS = {
+    # 4 processes x 8 local states (3 bits, one word), out-degree 1-3 over 6 labels,
+    # 2 labels as two-party rules between fixed pairs; 2^16-word table, 32-word buckets
+    "tiny": dict(seed=0, n_procs=4, n_states=8, deg_lo=1, deg_hi=3, n_labels=6, n_sync=2,
+                 parties=2, name="tiny_s0"),
+    # 10 processes x 16 local states (4 bits, 40 bits -> 2 words), out-degree 1-3,
+    # 12 labels of which 4 (30 %) are two-party rules; local edges stay in blocks of 8
+    # states; 2^28-word table
+    "mid": dict(seed=11, n_procs=10, n_states=16, deg_lo=1, deg_hi=3, n_labels=12, n_sync=4,
+                parties=2, cluster=8, name="mid_s11"),
+}
+
+
+def workload(name: str) -> Network:
+    return random_network(**WORKLOADS[name])
+
+
+# --------------------------------------------------------------------------------------------
 # Key sequences for the isolated hash-table experiment (Sec. 5.1)
 # --------------------------------------------------------------------------------------------
 

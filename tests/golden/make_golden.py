@@ -1,0 +1,41 @@
+"""Write the stored oracle results used by the GPU parity tests and the bench.
+
+    python tests/golden/make_golden.py mid        # ~5 min, ~6 GB host RAM
+
+Every value written here comes from the CPU oracle (oracle/) run on a network
+drawn by paper_1801_05857_gb300.inputs; nothing comes from the CUDA path.
+"""
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_1801_05857_gb300 import inputs  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# Mid network: inputs.WORKLOADS["mid"] (10 x 16 states, 2-word vectors, 4 two-party rules)
+MID = inputs.WORKLOADS["mid"]
+
+
+def write(name: str, gen: dict) -> None:
+    net = inputs.random_network(**gen)
+    r = oracle.explore(net, deadlocks_cap=1 << 12)
+    assert r.complete
+    out = dict(generator=gen, states=r.states, transitions=r.transitions, levels=r.levels,
+               deadlock_count=r.deadlock_count, deadlock_sum=r.deadlock_sum,
+               deadlock_xor=r.deadlock_xor, set_sum=r.set_sum, set_xor=r.set_xor,
+               oracle_seconds=round(r.seconds, 2),
+               note="written by tests/golden/make_golden.py from oracle.explore")
+    with open(os.path.join(HERE, name), "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, r.states, r.transitions, len(r.levels), round(r.seconds, 1), "s")
+
+
+if __name__ == "__main__":
+    which = sys.argv[1:] or ["mid"]
+    if "mid" in which:
+        write("mid_network.json", MID)

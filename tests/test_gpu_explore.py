@@ -1,0 +1,202 @@
+"""Parity of the CUDA exploration path with the CPU oracle (through the C ABI).
+
+Bit-exact on: reachable-state count, transition count, every BFS level size,
+deadlock count and order-free deadlock digest, and the digest of the whole
+reachable set read back from the hash table.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1801_05857_gb300 import gx, inputs
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def run_gpu(net, **opts):
+    import torch
+    h = gx.load_network(net)
+    o = gx.default_opts(**opts)
+    ws = gx.alloc_workspace(h, o)
+    gx.explore(h, o, ws)
+    torch.cuda.synchronize()
+    return h, gx.stats(h), gx.levels(h), ws
+
+
+def assert_parity(net, check_set=True, **opts):
+    r = oracle.explore(net, deadlocks_cap=1 << 14)
+    h, s, lv, ws = run_gpu(net, **opts)
+    assert s["status"] == 0 and s["complete"] == 1
+    assert s["states"] == r.states
+    assert s["transitions"] == r.transitions
+    assert lv == r.levels
+    assert s["explored"] == r.explored
+    assert s["deadlock_count"] == r.deadlock_count
+    assert s["deadlock_sum"] == r.deadlock_sum
+    assert s["deadlock_xor"] == r.deadlock_xor
+    if check_set:
+        c, ssum, sxor = gx.set_digest(h, ws)
+        assert (c, ssum, sxor) == (r.states, r.set_sum, r.set_xor)
+    if 0 < r.deadlock_count <= 1024:
+        got = {tuple(x) for x in gx.deadlocks(h)}
+        assert got == {tuple(x) for x in r.deadlocks}
+    return s
+
+
+def test_fig1(cuda):
+    s = assert_parity(inputs.producer_consumers(), table_bytes=1 << 16)
+    assert s["states"] == 8 and s["transitions"] == 24
+
+
+@pytest.mark.parametrize("n_nodes", list(range(2, 13)))
+def test_token_ring(cuda, n_nodes):
+    s = assert_parity(inputs.token_ring(n_nodes), table_bytes=1 << 26)
+    assert s["vector_words"] == (1 if n_nodes <= 10 else 2)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_tiny_config(cuda, seed):
+    # 4 processes x 8 states, out-degree 1-3 over 6 labels, 2 two-party rules; 2^16-word table, B=32
+    net = inputs.random_network(seed, 4, 8, 1, 3, 6, n_sync=2, parties=2)
+    assert_parity(net, table_bytes=4 << 16, bucket_words=32)
+
+
+def _nets_by_width():
+    return {
+        1: inputs.random_network(7, 6, 8, 1, 3, 8, n_sync=2, parties=2),
+        2: inputs.random_network(1, 10, 16, 1, 3, 12, n_sync=4, parties=2, cluster=4),
+        4: inputs.random_network(0, 13, 64, 1, 3, 16, n_sync=8, parties=3, cluster=4),
+    }
+
+
+@pytest.mark.parametrize("W", [1, 2, 4])
+def test_every_bucket_and_group_size(cuda, W):
+    net = _nets_by_width()[W]
+    r = oracle.explore(net)
+    assert 1000 < r.states < 5_000_000
+    for B in (4, 8, 16, 32):
+        if B < W:
+            continue
+        G = 1
+        while G <= B // W and G <= 32:
+            h, s, lv, ws = run_gpu(net, bucket_words=B, group_lanes=G, hash_rounds=32,
+                                   table_bytes=1 << 26)
+            assert s["slot_words"] == W
+            assert (s["states"], s["transitions"], lv) == (r.states, r.transitions, r.levels), (B, G)
+            assert (s["deadlock_count"], s["deadlock_sum"]) == (r.deadlock_count, r.deadlock_sum)
+            G *= 2
+
+
+@pytest.mark.parametrize("net", [
+    inputs.random_network(s, 13, 64, 1, 3, 16, n_sync=8, parties=3, cluster=4) for s in range(3)] + [
+    inputs.random_network(0, 20, 16, 1, 3, 20, n_sync=8, parties=3, cluster=2)], ids=lambda n: n.name)
+def test_three_party_four_words(cuda, net):
+    s = assert_parity(net, table_bytes=1 << 26)
+    assert s["slot_words"] == 4
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_deadlock_networks(cuda, seed):
+    net = inputs.random_network(seed, 8, 8, 0, 2, 10, n_sync=4, parties=2)
+    assert_parity(net, table_bytes=1 << 22)
+    net = inputs.random_network(seed, 4, 5, 0, 2, 6, n_sync=2, parties=2)
+    assert_parity(net, table_bytes=1 << 22)
+
+
+def test_bfs_first_deadlock_mode(cuda):
+    checked = 0
+    for seed in range(30):
+        net = inputs.random_network(seed, 4, 5, 0, 2, 6, n_sync=2, parties=2)
+        r = oracle.explore(net, stop_at_first_deadlock=True)
+        if r.deadlock_count == 0:
+            continue
+        h = gx.load_network(net)
+        o = gx.default_opts(table_bytes=1 << 22)
+        ws = gx.alloc_workspace(h, o)
+        n, states = gx.find_deadlocks(h, gx.GX_DL_BFS_FIRST, o, ws)
+        s = gx.stats(h)
+        assert n == r.deadlock_count
+        assert s["first_deadlock_level"] == r.first_deadlock_level
+        assert gx.levels(h) == r.levels
+        assert s["explored"] == r.explored and s["transitions"] == r.transitions
+        assert {tuple(x) for x in states} == {tuple(x) for x in r.deadlocks}
+        # every reported state is a reachable deadlock: no successor in the oracle
+        for x in states:
+            assert len(oracle.successors(net, x)) == 0
+        checked += 1
+    assert checked >= 3
+
+
+def test_table_full_is_reported(cuda):
+    h = gx.load_network(inputs.token_ring(8))
+    o = gx.default_opts(table_bytes=4096, bucket_words=8)
+    ws = gx.alloc_workspace(h, o)
+    with pytest.raises(gx.GxError) as e:
+        gx.explore(h, o, ws)
+    assert e.value.status == gx.GX_ERR_TABLE_FULL
+    s = gx.stats(h)
+    assert s["complete"] == 0 and s["status"] == gx.GX_ERR_TABLE_FULL
+
+
+def test_frontier_overflow_is_reported(cuda):
+    h = gx.load_network(inputs.token_ring(9))
+    o = gx.default_opts(table_bytes=1 << 24, frontier_states=64)
+    ws = gx.alloc_workspace(h, o)
+    with pytest.raises(gx.GxError) as e:
+        gx.explore(h, o, ws)
+    assert e.value.status == gx.GX_ERR_FRONTIER_OVERFLOW
+
+
+def test_workspace_too_small_and_library_allocation(cuda):
+    import torch
+    net = inputs.token_ring(6)
+    h = gx.load_network(net)
+    o = gx.default_opts(table_bytes=1 << 20)
+    small = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    with pytest.raises(gx.GxError) as e:
+        gx.explore(h, o, small)
+    assert e.value.status == gx.GX_ERR_OOM
+    gx.explore(h, o, None)  # library-owned workspace
+    assert gx.stats(h)["states"] == 2 * 6 * 3 ** 5
+
+
+def test_repeated_runs_identical(cuda):
+    net = inputs.random_network(1, 10, 16, 1, 3, 12, n_sync=4, parties=2, cluster=4)
+    h = gx.load_network(net)
+    o = gx.default_opts(table_bytes=1 << 26)
+    ws = gx.alloc_workspace(h, o)
+    out = []
+    for _ in range(3):
+        gx.explore(h, o, ws)
+        s = gx.stats(h)
+        out.append((s["states"], s["transitions"], tuple(gx.levels(h)), gx.set_digest(h, ws)))
+    assert out[0] == out[1] == out[2]
+
+
+def _golden_case(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        pytest.skip(f"{name} not generated")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("bucket", [32, 16, 8, 4])
+def test_mid_config_against_stored_oracle(cuda, bucket):
+    """Mid network (10 x 16 states, 2-word vectors, 12 labels with 4 two-party rules),
+    2^28-word table; expected values written by tests/golden/make_golden.py (oracle only)."""
+    g = _golden_case("mid_network.json")
+    net = inputs.random_network(**g["generator"])
+    h, s, lv, ws = run_gpu(net, table_bytes=4 << 28, bucket_words=bucket, hash_rounds=32)
+    assert s["states"] == g["states"]
+    assert s["transitions"] == g["transitions"]
+    assert lv == g["levels"]
+    assert (s["deadlock_count"], s["deadlock_sum"], s["deadlock_xor"]) == (
+        g["deadlock_count"], g["deadlock_sum"], g["deadlock_xor"])
+    assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])
+    assert s["fill"] <= 0.75
