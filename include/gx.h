@@ -195,6 +195,37 @@ gx_status gx_set_digest(gx_net* net, void* workspace, uint64_t workspace_bytes, 
                         uint64_t* count, uint64_t* sum, uint64_t* xr);
 
 /* ------------------------------------------------------------------------------------------
+ * Exploration that allocates nothing.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory -- a host
+ * framework that has reserved the GPU's memory for its own pool (cudaMalloc
+ * then fails or escapes its accounting), or a latency-critical caller that
+ * must not pay cudaFree's device-wide synchronisation.
+ *
+ * Same search as gx_explore, but all scratch (control block, network tables,
+ * frontier ring, hash table) lives in one static device array of
+ * GX_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
+ * library holds until the process exits.  No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ *   - Sizes: table_bytes 0 means 32 MiB; frontier_states as for gx_explore.
+ *     If table + frontier + tables exceed the array, GX_ERR_INVALID is
+ *     returned with the sizes in the message.
+ *   - Outputs: *stats_out (gpu_ms and expand_ms are 0: no events are
+ *     created); levels_out receives min(levels_cap, n) level sizes and
+ *     *n_levels (may be NULL) the total.  Deadlocks are counted and digested
+ *     but not stored.  Nothing is recorded in `net`.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture.
+ *   - Every call shares the array and it keeps the previous call's contents;
+ *     each call clears what must start at zero.  Calls whose device work
+ *     overlaps (two streams, two threads) race on the array.
+ * Synchronises `stream`. */
+#define GX_NOALLOC_SCRATCH_BYTES (64ull << 20)
+gx_status gx_explore_noalloc(const gx_net* net, const gx_explore_opts* opts, void* stream,
+                             gx_stats_t* stats_out, uint64_t* levels_out, uint32_t levels_cap,
+                             uint32_t* n_levels);
+
+/* ------------------------------------------------------------------------------------------
  * The isolated hash-table experiment (Sec. 5.1, Fig. "buckvsgputable"):
  * find-or-put of n_keys keys of key_words uint32 each into a table.
  *   keys:    device pointer, n_keys * key_words uint32, row-major; bit 31 of

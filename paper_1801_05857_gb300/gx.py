@@ -102,6 +102,8 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "gx_set_digest": ([vp, vp, u64, vp, P(u64), P(u64), P(u64)], ctypes.c_int),
         "gx_find_or_put": ([vp, u64, u32, u32, u32, u32, vp, u64, vp, vp, vp], ctypes.c_int),
         "gx_probe_random": ([u32, vp, u64, u64, u32, u64, vp, vp], ctypes.c_int),
+        "gx_explore_noalloc": ([vp, P(gx_explore_opts), vp, P(gx_stats_t), P(u64), u32, P(u32)],
+                               ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -267,6 +269,20 @@ def set_digest(net: Net, workspace, stream=None):
     _check(lib().gx_set_digest(net.handle, _ptr(workspace), workspace.numel(), _stream(stream),
                                ctypes.byref(c), ctypes.byref(s), ctypes.byref(x)))
     return int(c.value), int(s.value), int(x.value)
+
+
+def explore_noalloc(net: Net, opts: gx_explore_opts | None = None, stream=None,
+                    levels_cap: int = 1 << 16):
+    """gx_explore_noalloc: the search on the library's static scratch array (for
+    callers that cannot allocate device memory).  Returns (stats dict, level sizes)."""
+    s = gx_stats_t()
+    lv = np.zeros(max(levels_cap, 1), dtype=np.uint64)
+    n = u32()
+    _check(lib().gx_explore_noalloc(net.handle, ctypes.byref(opts) if opts else None,
+                                    _stream(stream), ctypes.byref(s), lv.ctypes.data_as(P(u64)),
+                                    levels_cap, ctypes.byref(n)))
+    stats_d = {name: getattr(s, name) for name, _ in gx_stats_t._fields_ if name != "reserved"}
+    return stats_d, [int(x) for x in lv[:min(int(n.value), levels_cap)]]
 
 
 # --------------------------------------------------------------------------------------------
