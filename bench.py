@@ -39,13 +39,17 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mid")
     ap.add_argument("--bucket", type=int, default=8)
-    ap.add_argument("--group", type=int, default=0)
+    ap.add_argument("--group", type=int, default=2)
     ap.add_argument("--rounds", type=int, default=32)
     ap.add_argument("--table-log2-words", type=int, default=28)
     ap.add_argument("--cpu-sample", type=int, default=3_000_000,
                     help="states the CPU baseline explores (bounded sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-table", action="store_true", help="skip the Sec. 5.1 find-or-put part")
+    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep"],
+                    help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
+                         "exploration for every (bucket, group) size; one JSON line per point")
     return ap.parse_args()
 
 
@@ -174,6 +178,45 @@ def random_access_peak(torch, gx) -> dict:
     return out
 
 
+def table_keys(torch, n: int, dup: int, seed: int = 0):
+    """Sec. 5.1 input on the device: n one-word keys, n // dup distinct, each repeated dup times."""
+    from paper_1801_05857_gb300 import inputs
+    return inputs.key_sequence_device(n, dup, seed=seed)
+
+
+def time_find_or_put(torch, gx, keys, words, table_words, bucket, group, rounds, reps=3):
+    """Median device time of inserting every key into an empty table (Sec. 5.1), and counters."""
+    st = torch.cuda.current_stream()
+    table = torch.zeros(table_words, dtype=torch.int32, device="cuda")
+    counters = torch.zeros(3, dtype=torch.int64, device="cuda")
+    times = []
+    for _ in range(reps + 1):
+        table.zero_()
+        counters.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        gx.find_or_put(keys, words, table, counters, None, bucket_words=bucket, group_lanes=group,
+                       hash_rounds=rounds)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    times = sorted(times[1:])
+    c = counters.cpu().tolist()
+    del table
+    return times[len(times) // 2], c
+
+
+def table_point(torch, gx, keys, n, dup, words, table_words, bucket, group, rounds, gather32):
+    ms, c = time_find_or_put(torch, gx, keys, words, table_words, bucket, group, rounds)
+    assert c[0] == n // dup and c[2] == 0, c
+    # algorithmic bytes: the key read, one sector per bucket read, one sector per claimed slot
+    bucket_bytes = max(32, 4 * bucket)
+    return {"keys": n, "dup": dup, "bucket_words": bucket, "group_lanes": group, "ms": round(ms, 3),
+            "Gkeys_per_s": round(n / (ms * 1e-3) / 1e9, 3),
+            "fill": round((n // dup) / (table_words // words), 4),
+            "frac_random_gather32": round((n / (ms * 1e-3)) / gather32, 4) if gather32 else None}
+
+
 def cpu_baseline(net, sample: int) -> dict:
     import oracle
     r = oracle.explore(net, max_explored=sample)
@@ -276,6 +319,20 @@ def run_ours(args, world, rank, local, pg):
         roof["random_access_unit"] = "G accesses/s, GB/s"
         roof["probes_per_s"] = round(s_avg["probes"] / (exp_ms_per_search * 1e-3) / 1e9, 3)
 
+    # Sec. 5.1: 10^8 one-word keys into a 2^27-word table (74.5 % fill at duplication 1)
+    table_part = None
+    if rank == 0 and not args.no_table:
+        n = 100_000_000
+        g32 = roof.get("random_access", {}).get("gather32_per_s")
+        g32 = g32 * 1e9 if g32 else None
+        pts = []
+        for dup, bucket, group in ((1, 16, 2), (21, 8, 2)):
+            nd = n - n % dup
+            keys = table_keys(torch, nd, dup)
+            pts.append(table_point(torch, gx, keys, nd, dup, 1, 1 << 27, bucket, group, 32, g32))
+            del keys
+        table_part = {"keys": n, "key_words": 1, "table_words": 1 << 27, "points": pts}
+
     # end to end through the public API with host-resident inputs: load the network
     # description from host arrays, explore with a library-allocated workspace, read the
     # results back to the host
@@ -317,6 +374,7 @@ def run_ours(args, world, rank, local, pg):
                        "parallelism": "replicas" if world > 1 else "single"},
             "transitions_per_s": round(tps, 1),
             "roofline": roof,
+            "find_or_put": table_part,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps * (1 + launches // args.steps),
@@ -325,8 +383,55 @@ def run_ours(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def run_experiment(args):
+    """One JSON line per point; not the bench contract's line."""
+    import torch
+    from paper_1801_05857_gb300 import gx, inputs
+    if args.experiment == "table-sweep":
+        n = 100_000_000
+        rp = random_access_peak(torch, gx)
+        g32 = rp["gather32_per_s"]
+        for dup in (1, 2, 5, 10, 21, 50, 100):
+            nd = n - n % dup
+            keys = table_keys(torch, nd, dup)
+            for bucket in (4, 8, 16, 32):
+                group = 1
+                while group <= bucket:
+                    pt = table_point(torch, gx, keys, nd, dup, 1, 1 << 27, bucket, group, 32, g32)
+                    print(json.dumps({"experiment": "sec5.1 find-or-put", **pt}), flush=True)
+                    group *= 2
+            del keys
+    elif args.experiment == "bucket-sweep":
+        net = inputs.workload(args.workload)
+        h = gx.load_network(net)
+        W = gx.layout(h)["vector_words"]
+        for bucket in (4, 8, 16, 32):
+            group = 1
+            while bucket >= W and group <= bucket // W:
+                o = gx.default_opts(bucket_words=bucket, group_lanes=group, hash_rounds=args.rounds,
+                                    table_bytes=4 << args.table_log2_words)
+                ws = gx.alloc_workspace(h, o)
+                ts = []
+                for _ in range(args.warmup + args.steps):
+                    gx.explore(h, o, ws)
+                    ts.append(gx.stats(h)["gpu_ms"])
+                ts = sorted(ts[args.warmup:])
+                s = gx.stats(h)
+                print(json.dumps({"experiment": "bucket-sweep", "workload": args.workload,
+                                  "bucket_words": bucket, "group_lanes": group,
+                                  "ms_median": round(ts[len(ts) // 2], 3), "states": s["states"],
+                                  "probes_per_successor": round(s["probes"] / s["transitions"], 4)}),
+                      flush=True)
+                del ws
+                torch.cuda.empty_cache()
+                group *= 2
+
+
 def main():
     args = parse()
+    if args.experiment:
+        run_experiment(args)
+        return
     world, rank, local, pg = dist_setup()
     try:
         if args.impl == "reference":

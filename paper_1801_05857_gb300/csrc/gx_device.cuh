@@ -71,15 +71,21 @@ __device__ __forceinline__ void load_words(const uint32_t* p, uint32_t (&s)[LW])
     uint2 x = __ldcg(reinterpret_cast<const uint2*>(p));
     s[0] = x.x;
     s[1] = x.y;
+  } else if constexpr (LW == 4) {
+    uint4 x = __ldcg(reinterpret_cast<const uint4*>(p));
+    s[0] = x.x;
+    s[1] = x.y;
+    s[2] = x.z;
+    s[3] = x.w;
   } else {
-    static_assert(LW % 4 == 0, "lane load width");
+    // 256-bit loads (sm_100 and later): one instruction per 32-byte sector
+    static_assert(LW % 8 == 0, "lane load width");
 #pragma unroll
-    for (int i = 0; i < LW / 4; ++i) {
-      uint4 x = __ldcg(reinterpret_cast<const uint4*>(p) + i);
-      s[4 * i + 0] = x.x;
-      s[4 * i + 1] = x.y;
-      s[4 * i + 2] = x.z;
-      s[4 * i + 3] = x.w;
+    for (int i = 0; i < LW / 8; ++i) {
+      asm volatile("ld.global.cg.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                   : "=r"(s[8 * i + 0]), "=r"(s[8 * i + 1]), "=r"(s[8 * i + 2]), "=r"(s[8 * i + 3]),
+                     "=r"(s[8 * i + 4]), "=r"(s[8 * i + 5]), "=r"(s[8 * i + 6]), "=r"(s[8 * i + 7])
+                   : "l"(p + 8 * i));
     }
   }
 }

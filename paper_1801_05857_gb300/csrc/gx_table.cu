@@ -9,29 +9,28 @@ namespace gxd {
 
 // Counter-based position stream: access i of a probe run goes to unit
 // mix64(seed + i) & (n_units - 1) (n_units a power of two), so every access is
-// independent.  Each thread keeps kInFlight accesses in flight.
-constexpr int kInFlight = 4;
-
+// independent.  Each thread keeps K accesses in flight; a unit is read with
+// 256-bit loads (one load for a 32-byte unit).
+template <int K, int UW>
 __global__ void __launch_bounds__(gx::kBlock)
-probe_gather_kernel(const uint32_t* __restrict__ buf, uint64_t unit_mask, int unit_words, uint64_t n,
-                    uint64_t seed, unsigned long long* sink) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * kInFlight;
+probe_gather_kernel(const uint32_t* __restrict__ buf, uint64_t unit_mask, uint64_t n, uint64_t seed,
+                    unsigned long long* sink) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * K;
   uint32_t acc = 0;
-  for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * kInFlight; i0 < n; i0 += stride) {
-    uint4 x[kInFlight][2];
+  for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * K; i0 < n; i0 += stride) {
+    uint32_t x[K][UW];
 #pragma unroll
-    for (int j = 0; j < kInFlight; ++j) {
+    for (int j = 0; j < K; ++j) {
       const uint64_t u = mix64(seed + i0 + j) & unit_mask;
-      const uint4* p = reinterpret_cast<const uint4*>(buf + u * unit_words);
-      x[j][0] = (i0 + j < n) ? __ldcg(p) : make_uint4(0, 0, 0, 0);
-      x[j][1] = (i0 + j < n && unit_words >= 8) ? __ldcg(p + 1) : make_uint4(0, 0, 0, 0);
-      for (int k = 2; k < unit_words / 4; ++k) {
-        const uint4 y = (i0 + j < n) ? __ldcg(p + k) : make_uint4(0, 0, 0, 0);
-        acc ^= y.x ^ y.w;
-      }
+      if (i0 + j < n) load_words<UW>(buf + u * UW, x[j]);
+      else
+#pragma unroll
+        for (int w = 0; w < UW; ++w) x[j][w] = 0;
     }
 #pragma unroll
-    for (int j = 0; j < kInFlight; ++j) acc ^= x[j][0].x ^ x[j][0].w ^ x[j][1].y ^ x[j][1].z;
+    for (int j = 0; j < K; ++j)
+#pragma unroll
+      for (int w = 0; w < UW; ++w) acc ^= x[j][w];
   }
   acc = __reduce_xor_sync(FULLMASK, acc);
   if ((threadIdx.x & 31) == 0 && acc) atomicXor(sink, (unsigned long long)acc);
@@ -148,10 +147,14 @@ gx_status gx_probe_random(uint32_t kind, uint32_t* buffer, uint64_t words, uint6
   if ((uint64_t)unit_words > words) return gx::fail(GX_ERR_INVALID, "buffer smaller than one access");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int grid = sm_count() * 8;
-  if (kind == 0)
-    gxd::probe_gather_kernel<<<grid, gx::kBlock, 0, st>>>(buffer, n_units - 1, unit_words, n, seed,
-                                                          reinterpret_cast<unsigned long long*>(sink));
-  else
+  unsigned long long* sk = reinterpret_cast<unsigned long long*>(sink);
+  if (kind == 0) {
+    // 4 accesses in flight per thread for small units, 2 for 64/128-byte units
+    if (unit_words == 4) gxd::probe_gather_kernel<4, 4><<<grid, gx::kBlock, 0, st>>>(buffer, n_units - 1, n, seed, sk);
+    else if (unit_words == 8) gxd::probe_gather_kernel<4, 8><<<grid, gx::kBlock, 0, st>>>(buffer, n_units - 1, n, seed, sk);
+    else if (unit_words == 16) gxd::probe_gather_kernel<2, 16><<<grid, gx::kBlock, 0, st>>>(buffer, n_units - 1, n, seed, sk);
+    else gxd::probe_gather_kernel<2, 32><<<grid, gx::kBlock, 0, st>>>(buffer, n_units - 1, n, seed, sk);
+  } else
     gxd::probe_cas_kernel<<<grid, gx::kBlock, 0, st>>>(buffer, n_units - 1, unit_words, n, seed,
                                                        reinterpret_cast<unsigned long long*>(sink));
   cudaError_t e = cudaGetLastError();

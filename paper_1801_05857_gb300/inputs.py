@@ -296,3 +296,30 @@ def key_sequence(n: int, duplication: int, words: int = 1, seed: int = 0) -> np.
     uniq = np.stack(cols, axis=1)
     order = np.random.Generator(np.random.PCG64(seed)).permutation(n) % u
     return np.ascontiguousarray(uniq[order])
+
+
+def key_sequence_device(n: int, duplication: int, seed: int = 0, device="cuda"):
+    """The same distinct keys as key_sequence(words=1), generated on a torch device.
+
+    The order comes from torch.randperm with a seeded generator instead of
+    numpy's PCG64, so it differs from key_sequence's order; the multiset of keys
+    is identical.  Returns an int32 tensor of n keys (bit patterns of uint32).
+    """
+    import torch
+    assert n % duplication == 0
+    u = n // duplication
+    m = (1 << 31) - 1
+
+    def mix31(i):
+        x = (i + (seed & 0x7FFFFFFF)) & m
+        for mul in (0x2C1B3C6D, 0x297A2D39, 0x7FEB352D):
+            x = (x * (mul | 1)) & m
+            x = x ^ (x >> 15)
+        return x
+
+    w0 = mix31(torch.arange(u, dtype=torch.int64, device=device))
+    w0 = torch.where(w0 == 0, mix31(torch.tensor([u], dtype=torch.int64, device=device)), w0)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    order = torch.randperm(n, generator=g, device=device) % u
+    return w0[order].to(torch.int32)

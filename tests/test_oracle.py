@@ -225,3 +225,11 @@ def test_key_sequence_duplication():
     k4 = inputs.key_sequence(1000, 4, words=4, seed=1)
     u = np.unique(k4, axis=0)
     assert len(u) == 250 and ((k4 >> 31) == 0).all()
+
+
+def test_device_key_sequence_has_the_same_keys():
+    pytest.importorskip("torch")
+    for d in (1, 7, 21):
+        a = inputs.key_sequence_device(2100, d, seed=5, device="cpu").numpy().view(np.uint32)
+        b = inputs.key_sequence(2100, d, words=1, seed=5)[:, 0]
+        assert sorted(a.tolist()) == sorted(b.tolist())
