@@ -39,9 +39,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="mid")
     ap.add_argument("--bucket", type=int, default=8)
-    ap.add_argument("--group", type=int, default=2)
+    ap.add_argument("--group", type=int, default=1)
     ap.add_argument("--rounds", type=int, default=32)
     ap.add_argument("--table-log2-words", type=int, default=28)
+    ap.add_argument("--slice-log2", type=int, default=0)
+    ap.add_argument("--partition-min", type=int, default=0,
+                    help="partition levels with at least this many states (0 = never)")
     ap.add_argument("--cpu-sample", type=int, default=3_000_000,
                     help="states the CPU baseline explores (bounded sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -264,7 +267,8 @@ def run_ours(args, world, rank, local, pg):
     h = gx.load_network(net)
     table_bytes = 4 << args.table_log2_words
     opts = gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
-                           table_bytes=table_bytes)
+                           table_bytes=table_bytes, slice_log2=args.slice_log2,
+                           partition_min_states=args.partition_min)
     ws = gx.alloc_workspace(h, opts)
     st = torch.cuda.current_stream()
 
@@ -370,6 +374,7 @@ def run_ours(args, world, rank, local, pg):
                        "vector_words": s["vector_words"], "bucket_words": s["bucket_words"],
                        "group_lanes": s["group_lanes"], "hash_rounds": s["hash_rounds"],
                        "table_words": 1 << args.table_log2_words, "fill": round(s["fill"], 4),
+                       "partitioned_levels": s["partitioned_levels"],
                        "l2": "1 GiB table > 129 MB L2 (no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "transitions_per_s": round(tps, 1),

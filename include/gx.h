@@ -117,14 +117,24 @@ typedef struct gx_explore_opts {
                               buckets.  0 = 1 GiB */
   uint64_t frontier_states;/* capacity of the frontier ring in vectors; rounded up to a
                               power of two.  0 = table slots / 4 (at least 4096) */
+  /* Partitioned expansion (a slice-ordered form of the paper's batched flush of
+   * new vectors into the table, Sec. 3): a level's successors are counted per
+   * table slice, written slice by slice into a buffer and then looked up slice
+   * by slice, so the part of the table being probed stays in L2.  Off by
+   * default: on the networks measured so far the direct path is faster. */
+  uint64_t successor_buffer;     /* buffer capacity in vectors (< 2^32); 0 = table slots / 2 */
+  uint32_t slice_log2;           /* 2^slice_log2 table slices; 0 = auto (about 32 MiB each,
+                                    at most 4096 slices) */
+  uint32_t partition_min_states; /* levels with at least this many states are partitioned;
+                                    0 = never (default) */
 } gx_explore_opts;
 
 /* Fill *opts with the defaults described above. */
 gx_status gx_default_opts(gx_explore_opts* opts);
 
 /* Bytes of device workspace gx_explore needs for this network and options
- * (table + frontier ring + control block + deadlock buffer + network tables).
- * When opts->table_bytes is 0 the table gets 1 GiB. */
+ * (table + frontier ring + successor buffer + control block + deadlock buffer
+ * + network tables).  When opts->table_bytes is 0 the table gets 1 GiB. */
 gx_status gx_workspace_bytes(const gx_net* net, const gx_explore_opts* opts, uint64_t* bytes);
 
 /* Full breadth-first exploration from the initial state (Sec. 3; the table
@@ -176,6 +186,7 @@ typedef struct gx_stats_t {
   uint64_t probes;          /* buckets read by find-or-put during the search */
   uint64_t h2d_bytes;       /* host-to-device bytes the search copied (network tables) */
   uint64_t d2h_bytes;       /* device-to-host bytes it copied (progress, deadlock states) */
+  uint64_t partitioned_levels; /* levels expanded by the partitioned path */
 } gx_stats_t;
 
 gx_status gx_stats(const gx_net* net, gx_stats_t* out);

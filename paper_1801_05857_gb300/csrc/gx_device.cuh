@@ -156,11 +156,13 @@ struct Group {
 // FOP_FULL (no free slot under any of the `rounds` hash-constant sets), the
 // same value in every lane of the group.  `probes` of the group's first lane
 // is increased by the number of buckets read (once per bucket, not per lane).
-template <int W, int B, int G>
-__device__ __forceinline__ int find_or_put(uint32_t* __restrict__ table, int log2nb, int rounds,
-                                           const uint64_t* __restrict__ muls,
-                                           const uint32_t (&v)[W], const Group<G>& g,
-                                           uint32_t& probes) {
+// With PRE, `pre` already holds this lane's part of the first bucket (read by
+// the caller, and counted there), so round 0 starts without a load.
+template <int W, int B, int G, bool PRE>
+__device__ __forceinline__ int find_or_put_from(uint32_t* __restrict__ table, int log2nb, int rounds,
+                                                const uint64_t* __restrict__ muls,
+                                                const uint32_t (&v)[W], const Group<G>& g,
+                                                uint32_t& probes, const uint32_t (&pre)[(B / W / G) * W]) {
   constexpr int S = B / W;
   static_assert(S >= 1 && S % G == 0, "group size must divide the slots per bucket");
   constexpr int SPL = S / G;
@@ -170,8 +172,13 @@ __device__ __forceinline__ int find_or_put(uint32_t* __restrict__ table, int log
     const uint64_t b = bucket_of(h, muls[k], log2nb);
     uint32_t* lane_slots = table + b * (uint64_t)B + (uint64_t)g.glane * LW;
     uint32_t s[LW];
-    load_words<LW>(lane_slots, s);
-    probes += g.glane == 0;
+    if (PRE && k == 0) {
+#pragma unroll
+      for (int i = 0; i < LW; ++i) s[i] = pre[i];
+    } else {
+      load_words<LW>(lane_slots, s);
+      probes += g.glane == 0;
+    }
     bool match = false;
     uint32_t cand = 0;  // slots that are empty or half-written
 #pragma unroll
@@ -211,6 +218,15 @@ __device__ __forceinline__ int find_or_put(uint32_t* __restrict__ table, int log
     }
   }
   return FOP_FULL;
+}
+
+template <int W, int B, int G>
+__device__ __forceinline__ int find_or_put(uint32_t* __restrict__ table, int log2nb, int rounds,
+                                           const uint64_t* __restrict__ muls,
+                                           const uint32_t (&v)[W], const Group<G>& g,
+                                           uint32_t& probes) {
+  const uint32_t none[(B / W / G) * W] = {};
+  return find_or_put_from<W, B, G, false>(table, log2nb, rounds, muls, v, g, probes, none);
 }
 
 // ---- vector fields

@@ -107,12 +107,18 @@ inline int ilog2(uint64_t x) {
       return gx::fail(GX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
   } while (0)
 
+constexpr int kPartCtas = 1024;  // CTAs of the partitioned count/scatter passes (at most)
+
 struct Plan {
   int W = 0, B = 0, G = 0, rounds = 0;
   uint32_t dl_cap = 0;
   uint64_t nb = 0;         // buckets (power of two)
   uint64_t fcap = 0;       // frontier ring capacity (power of two)
+  int logp = 0;            // table slices for the partitioned path (0 = path off)
+  uint64_t cs = 0;         // successor buffer capacity (vectors)
+  uint64_t part_min = 0;   // smallest level that may use the partitioned path
   uint64_t off_ctl = 0, off_blob = 0, off_dl = 0, off_front = 0, off_table = 0;
+  uint64_t off_hist = 0, off_off = 0, off_ptot = 0, off_tot = 0, off_succ = 0;
   uint64_t total = 0;
   const KernelSet* ks = nullptr;
 };
@@ -144,6 +150,21 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
   const uint64_t slots = P.nb * (uint64_t)S;
   P.fcap = pow2_ceil(o->frontier_states ? o->frontier_states : std::max<uint64_t>(4096, slots / 4));
   P.dl_cap = o->deadlock_cap ? o->deadlock_cap : 1024;
+  // partitioned path: slices of about 32 MiB, at most 4096 of them
+  const uint64_t tbytes = 4ull * P.B * P.nb;
+  if (o->slice_log2) {
+    if (o->slice_log2 > 12) return fail(GX_ERR_INVALID, "slice_log2 must be at most 12");
+    P.logp = (int)o->slice_log2;
+  } else {
+    P.logp = 0;
+    while (P.logp < 12 && (tbytes >> (P.logp + 1)) >= (32ull << 20)) ++P.logp;
+  }
+  if ((1ull << P.logp) > P.nb) P.logp = ilog2(P.nb);
+  P.part_min = o->partition_min_states;
+  if (P.part_min == 0) P.logp = 0;  // path off
+  P.cs = o->successor_buffer ? o->successor_buffer : slots / 2;
+  if (P.cs >= (1ull << 32)) return fail(GX_ERR_INVALID, "successor_buffer must be below 2^32 vectors");
+  if (P.logp == 0) P.cs = 0;
   uint64_t off = 0;
   P.off_ctl = off;
   off = align_up(off + sizeof(Ctl));
@@ -155,6 +176,17 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
   off = align_up(off + 4ull * P.W * P.fcap);
   P.off_table = off;
   off = align_up(off + 4ull * P.B * P.nb);
+  const uint64_t np = P.logp ? (1ull << P.logp) : 0;
+  P.off_hist = off;
+  off = align_up(off + 4ull * kPartCtas * np);
+  P.off_off = off;
+  off = align_up(off + 4ull * kPartCtas * np);
+  P.off_ptot = off;
+  off = align_up(off + 4ull * np);
+  P.off_tot = off;
+  off = align_up(off + (np ? 4ull * kPartCtas : 0));
+  P.off_succ = off;
+  off = align_up(off + 4ull * P.W * P.cs);
   P.total = off;
   return GX_OK;
 }
@@ -174,18 +206,23 @@ gx_status device_info(Device& d) {
   return GX_OK;
 }
 
-// Pinned host copy of the control block, one per thread.
+// Pinned host copies of the control block and of the per-CTA successor
+// totals of the partitioned path, one set per thread.
 struct HostCtl {
   Ctl* p = nullptr;
+  uint32_t* tot = nullptr;
   ~HostCtl() {
     if (p) cudaFreeHost(p);
+    if (tot) cudaFreeHost(tot);
   }
 };
 thread_local HostCtl g_hctl;
 
-gx_status host_ctl(Ctl*& out) {
+gx_status host_ctl(Ctl*& out, uint32_t*& tot) {
   if (!g_hctl.p) GX_CUDA(cudaMallocHost(reinterpret_cast<void**>(&g_hctl.p), sizeof(Ctl)));
+  if (!g_hctl.tot) GX_CUDA(cudaMallocHost(reinterpret_cast<void**>(&g_hctl.tot), 4ull * kPartCtas));
   out = g_hctl.p;
+  tot = g_hctl.tot;
   return GX_OK;
 }
 
@@ -201,7 +238,8 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   Device dev;
   if ((s = device_info(dev)) != GX_OK) return s;
   Ctl* hc = nullptr;
-  if ((s = host_ctl(hc)) != GX_OK) return s;
+  uint32_t* htot = nullptr;
+  if ((s = host_ctl(hc, htot)) != GX_OK) return s;
 
   bool owned = false;
   if (!ws) {
@@ -288,25 +326,80 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   uint64_t cur_begin = 0, cur_end = 1, explored = 0;
   int64_t first_dl = -1;
   double expand_ms = 0;
-  uint64_t launches = 0;
+  uint64_t launches = 0, levels_done = 0;
   uint32_t err = 0;
   bool complete = false;
+  // partitioned path set-up
+  PartArgs pa{};
+  size_t psmem = 0;
+  int probe_grid = 0;
+  if (P.logp) {
+    pa.hist = reinterpret_cast<uint32_t*>(base + P.off_hist);
+    pa.off = reinterpret_cast<uint32_t*>(base + P.off_off);
+    pa.ptot = reinterpret_cast<uint32_t*>(base + P.off_ptot);
+    pa.tot = reinterpret_cast<uint32_t*>(base + P.off_tot);
+    pa.succ = reinterpret_cast<uint32_t*>(base + P.off_succ);
+    pa.logp = P.logp;
+    psmem = 8ull * kMaxRounds + (ea.stage ? blob_bytes : 0) + (4ull << P.logp);
+    GX_CUDA(cudaFuncSetAttribute(P.ks->part_count_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+    GX_CUDA(cudaFuncSetAttribute(P.ks->part_scatter_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+    int pp = 0;
+    GX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pp, P.ks->part_probe_fn, kBlock, 0));
+    probe_grid = dev.sms * std::max(pp, 1);
+  }
+  uint64_t part_levels = 0, d2h_tot = 0;
+
   while (true) {
-    GX_CUDA(cudaMemsetAsync(&ctl->claim, 0, sizeof(unsigned long long), st));
+    const uint64_t F = cur_end - cur_begin;
     ea.cur_begin = cur_begin;
     ea.cur_end = cur_end;
-    const uint64_t warps = (cur_end - cur_begin + 31) / 32;
-    const uint64_t want = (warps + kBlock / 32 - 1) / (kBlock / 32);
-    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, max_grid));
+    const bool part = P.logp && F >= P.part_min;
     GX_CUDA(cudaEventRecord(ek0, st));
-    GX_CUDA(P.ks->expand(ea, grid, smem, st));
+    bool direct = !part;
+    if (part) {
+      pa.nb = (int)std::max<uint64_t>(1, std::min<uint64_t>(kPartCtas, F / kBlock));
+      pa.range = (F + pa.nb - 1) / pa.nb;
+      GX_CUDA(P.ks->part_count(ea, pa, psmem, st));
+      ++launches;
+      GX_CUDA(cudaMemcpyAsync(htot, pa.tot, 4ull * pa.nb, cudaMemcpyDeviceToHost, st));
+      d2h_tot += 4ull * pa.nb;
+      GX_CUDA(cudaStreamSynchronize(st));
+      uint32_t biggest = 0;
+      for (int b = 0; b < pa.nb; ++b) biggest = std::max(biggest, htot[b]);
+      direct = biggest > P.cs;  // one CTA's successors do not fit: expand this level directly
+      if (!direct) {
+        ++part_levels;
+        int b0 = 0;
+        while (b0 < pa.nb) {
+          uint64_t n = 0;
+          int b1 = b0;
+          while (b1 < pa.nb && n + htot[b1] <= P.cs) n += htot[b1++];
+          pa.b0 = b0;
+          pa.b1 = b1;
+          GX_CUDA(P.ks->part_scan(pa, st));
+          GX_CUDA(P.ks->part_scatter(ea, pa, psmem, st));
+          GX_CUDA(cudaMemsetAsync(&ctl->claim, 0, sizeof(unsigned long long), st));
+          GX_CUDA(P.ks->part_probe(ea, pa.succ, n, probe_grid, st));
+          launches += 3;
+          b0 = b1;
+        }
+      }
+    }
+    if (direct) {
+      GX_CUDA(cudaMemsetAsync(&ctl->claim, 0, sizeof(unsigned long long), st));
+      const uint64_t warps = (F + 31) / 32;
+      const uint64_t want = (warps + kBlock / 32 - 1) / (kBlock / 32);
+      const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, max_grid));
+      GX_CUDA(P.ks->expand(ea, grid, smem, st));
+      ++launches;
+    }
     GX_CUDA(cudaEventRecord(ek1, st));
     GX_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
     GX_CUDA(cudaStreamSynchronize(st));
     float ms = 0;
     GX_CUDA(cudaEventElapsedTime(&ms, ek0, ek1));
     expand_ms += ms;
-    ++launches;
+    ++levels_done;
     explored += cur_end - cur_begin;
     if (first_dl < 0 && hc->dl_count > 0) first_dl = (int64_t)levels.size() - 1;
     err = hc->error;
@@ -320,7 +413,7 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
     cur_begin = cur_end;
     cur_end = next_end;
     if (stop_first && hc->dl_count > 0) break;
-    if (o->max_levels && launches >= o->max_levels) break;
+    if (o->max_levels && levels_done >= o->max_levels) break;
   }
   GX_CUDA(cudaEventRecord(ev1, st));
   GX_CUDA(cudaStreamSynchronize(st));
@@ -363,8 +456,9 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   S.expand_ms = expand_ms;
   S.expand_launches = launches;
   S.probes = hc->probes;
+  S.partitioned_levels = part_levels;
   S.h2d_bytes = 4ull * net.blob.size();
-  S.d2h_bytes = sizeof(Ctl) * launches + 4ull * dlw.size();
+  S.d2h_bytes = sizeof(Ctl) * levels_done + 4ull * dlw.size() + d2h_tot;
   h->levels = levels;
   h->ws_off_ctl = P.off_ctl;
   h->ws_off_blob = P.off_blob;

@@ -167,6 +167,124 @@ __device__ __forceinline__ const uint32_t* stage_tables(uint32_t* sm, const gx::
   return s_tab;
 }
 
+// Per-warp staging of new vectors in shared memory: lanes that inserted a
+// vector append it here (ballot + popc, no atomic); every 32 staged vectors
+// are written to the next level with one global atomicAdd and one coalesced
+// store.  flush() writes what is left.  All 32 lanes call push/flush together.
+constexpr int kStage = 64;  // vectors per warp (at most 31 + 32 are ever staged)
+
+struct WarpStage {
+  uint32_t* buf;  // kStage * W words of this warp
+  int n;          // staged vectors (uniform in the warp)
+
+  template <int W>
+  __device__ __forceinline__ void write_out(const gx::ExpandArgs& a, int m, uint32_t& err) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&a.ctl->next_end, (unsigned long long)m);
+    base = __shfl_sync(FULLMASK, base, 0);
+    if (lane < m) {
+      const uint64_t pos = base + lane;
+      uint32_t v[W];
+#pragma unroll
+      for (int w = 0; w < W; ++w) v[w] = buf[lane * W + w];
+      if (pos - a.cur_begin <= a.fmask) store_vec<W>(a.frontier + (pos & a.fmask) * W, v);
+      else err |= gx::ERR_FRONTIER;
+    }
+  }
+
+  template <int W>
+  __device__ __forceinline__ void push(const gx::ExpandArgs& a, bool ins, const uint32_t (&v)[W],
+                                       uint32_t& err) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t im = __ballot_sync(FULLMASK, ins);
+    if (ins) {
+      const int at = n + __popc(im & ((1u << lane) - 1u));
+#pragma unroll
+      for (int w = 0; w < W; ++w) buf[at * W + w] = v[w];
+    }
+    n += __popc(im);
+    if (n >= 32) {
+      __syncwarp();
+      write_out<W>(a, 32, err);
+      __syncwarp();
+      // move the remainder (fewer than 32) to the front
+      if (lane < n - 32) {
+#pragma unroll
+        for (int w = 0; w < W; ++w) buf[lane * W + w] = buf[(32 + lane) * W + w];
+      }
+      n -= 32;
+      __syncwarp();
+    }
+  }
+
+  template <int W>
+  __device__ __forceinline__ void flush(const gx::ExpandArgs& a, uint32_t& err) {
+    __syncwarp();
+    if (n > 0) write_out<W>(a, n, err);
+    n = 0;
+    __syncwarp();
+  }
+};
+
+// Successors each lane generates per round.  insert_lanes takes K per lane
+// (the group issues the first-bucket loads of up to four items before it
+// resolves any of them); measured on the mid network, K = 2 or 4 costs more in
+// registers and occupancy than it gains in loads in flight, so K = 1.
+template <int G>
+struct PerLane {
+  static constexpr int K = 1;
+};
+
+// Find-or-put of the K vectors each lane holds (has[k]: lane holds vector k),
+// G lanes per bucket.  Phase 1 issues the first-bucket loads of all G*K items
+// of the group; phase 2 resolves them in order (found in the first bucket, or
+// the full find-or-put with the CAS and further rounds).  Vectors this call
+// inserted go to the warp's staging buffer.
+// Must be called by all 32 lanes of the warp together.
+template <int W, int B, int G, int K>
+__device__ __forceinline__ void insert_lanes(const gx::ExpandArgs& a, const uint64_t* muls,
+                                             const Group<G>& g, const bool (&has)[K],
+                                             const uint32_t (&s)[K][W], uint32_t& probes,
+                                             uint32_t& err, WarpStage& st) {
+  constexpr int LW = (B / W / G) * W;
+  constexpr int NI = G * K;            // items of the group this round
+  constexpr int CH = NI < 4 ? NI : 4;  // items in flight at a time
+  bool inserted[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) inserted[k] = false;
+#pragma unroll 1
+  for (int c = 0; c < NI; c += CH) {
+    uint32_t x[CH][W];
+    uint32_t pre[CH][LW];
+    bool hv[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int i = c + j;
+      const int src = g.base + i / K;
+      hv[j] = g.template bcast<int>(has[i % K] ? 1 : 0, src) != 0;  // uniform in the group
+#pragma unroll
+      for (int w = 0; w < W; ++w) x[j][w] = g.template bcast<uint32_t>(s[i % K][w], src);
+      if (hv[j]) {
+        const uint64_t b = bucket_of(vec_hash<W>(x[j]), muls[0], a.log2nb);
+        load_words<LW>(a.table + b * (uint64_t)B + (uint64_t)g.glane * LW, pre[j]);
+        probes += g.glane == 0;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      if (!hv[j]) continue;
+      const int i = c + j;
+      const int r = find_or_put_from<W, B, G, true>(a.table, a.log2nb, a.rounds, muls, x[j], g, probes,
+                                                    pre[j]);
+      if (r == FOP_FULL) err |= gx::ERR_TABLE_FULL;
+      if (g.glane == i / K && r == FOP_INSERTED) inserted[i % K] = true;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) st.push<W>(a, inserted[k], s[k], err);
+}
+
 template <int W, int B, int G>
 __global__ void __launch_bounds__(gx::kBlock) expand_kernel(const gx::ExpandArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
@@ -178,6 +296,8 @@ __global__ void __launch_bounds__(gx::kBlock) expand_kernel(const gx::ExpandArgs
   const Group<G> g;
   unsigned long long trans = 0;
   uint32_t probes = 0, err = 0;
+  __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
+  WarpStage st{stage_mem[threadIdx.x >> 5], 0};
 
   while (true) {
     unsigned long long chunk = 0;
@@ -202,46 +322,218 @@ __global__ void __launch_bounds__(gx::kBlock) expand_kernel(const gx::ExpandArgs
     }
     SuccIter it;
     it.init();
+    constexpr int K = PerLane<G>::K;
     while (__any_sync(FULLMASK, remaining != 0)) {
-      uint32_t s[W];
-      const bool has = remaining != 0;
-      if (has) {
-        next_succ<W>(it, t, L, v, s);
-        --remaining;
-      } else {
+      uint32_t s[K][W];
+      bool has[K];
 #pragma unroll
-        for (int w = 0; w < W; ++w) s[w] = 0;
-      }
-      bool inserted = false;
-#pragma unroll 1
-      for (int l = 0; l < G; ++l) {
-        const int src = g.base + l;
-        if (!g.template bcast<int>(has ? 1 : 0, src)) continue;  // uniform in the group
-        uint32_t x[W];
+      for (int k = 0; k < K; ++k) {
+        has[k] = remaining != 0;
+        if (has[k]) {
+          next_succ<W>(it, t, L, v, s[k]);
+          --remaining;
+        } else {
 #pragma unroll
-        for (int w = 0; w < W; ++w) x[w] = g.template bcast<uint32_t>(s[w], src);
-        const int r = find_or_put<W, B, G>(a.table, a.log2nb, a.rounds, muls, x, g, probes);
-        if (r == FOP_FULL) err |= gx::ERR_TABLE_FULL;
-        if (g.glane == l && r == FOP_INSERTED) inserted = true;
-      }
-      const uint32_t im = __ballot_sync(FULLMASK, inserted);
-      if (im) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&a.ctl->next_end, (unsigned long long)__popc(im));
-        base = __shfl_sync(FULLMASK, base, 0);
-        if (inserted) {
-          const uint64_t pos = base + __popc(im & ((1u << lane) - 1u));
-          if (pos - a.cur_begin <= a.fmask) store_vec<W>(a.frontier + (pos & a.fmask) * W, s);
-          else err |= gx::ERR_FRONTIER;
+          for (int w = 0; w < W; ++w) s[k][w] = 0;
         }
       }
+      insert_lanes<W, B, G, K>(a, muls, g, has, s, probes, err, st);
     }
   }
+  st.flush<W>(a, err);
   trans = warp_sum(trans);
   const unsigned long long pr = warp_sum((unsigned long long)probes);
   err = __reduce_or_sync(FULLMASK, err);
   if (lane == 0) {
     if (trans) atomicAdd(&a.ctl->transitions, trans);
+    if (pr) atomicAdd(&a.ctl->probes, pr);
+    if (err) atomicOr(&a.ctl->error, err);
+  }
+}
+
+
+// ---- partitioned expansion (see PartArgs)
+
+// Exclusive scan of one value per thread over the block (blockDim.x == kBlock).
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t& total, uint32_t* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULLMASK, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) scratch[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = lane < (gx::kBlock / 32) ? scratch[lane] : 0u;
+    uint32_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULLMASK, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < (gx::kBlock / 32)) scratch[lane] = wi - w;  // exclusive warp offsets
+    if (lane == (gx::kBlock / 32) - 1) scratch[gx::kBlock / 32] = wi;
+  }
+  __syncthreads();
+  const uint32_t r = scratch[wid] + inc - x;
+  total = scratch[gx::kBlock / 32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void part_range(const gx::ExpandArgs& a, const gx::PartArgs& pa, int b,
+                                           uint64_t& lo, uint64_t& hi) {
+  lo = a.cur_begin + (uint64_t)b * pa.range;
+  hi = lo + pa.range;
+  if (hi > a.cur_end) hi = a.cur_end;
+  if (lo > hi) lo = hi;
+}
+
+// Pass 1: successors per (CTA, slice).  No other side effect, so a level may still
+// fall back to the direct kernel after it.
+template <int W>
+__global__ void __launch_bounds__(gx::kBlock) part_count_kernel(const gx::ExpandArgs a, const gx::PartArgs pa) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const uint64_t* muls;
+  const uint32_t* t = stage_tables(sm, a.muls, 1, a.blob, a.blob_words, a.stage, muls);
+  uint32_t* hist = sm + 2 * kMaxRounds + (a.stage ? a.blob_words : 0);
+  __shared__ uint32_t scan_scratch[gx::kBlock / 32 + 1];
+  const int P = 1 << pa.logp;
+  for (int q = threadIdx.x; q < P; q += blockDim.x) hist[q] = 0;
+  __syncthreads();
+  const NetBlobLayout& L = a.lay;
+  const uint64_t mul0 = muls[0];
+  const int shift = 64 - pa.logp;
+  uint64_t lo, hi;
+  part_range(a, pa, blockIdx.x, lo, hi);
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    uint32_t v[W];
+    load_vec<W>(a.frontier + (i & a.fmask) * W, v);
+    const uint32_t cnt = count_succ<W>(t, L, v);
+    SuccIter it;
+    it.init();
+    for (uint32_t k = 0; k < cnt; ++k) {
+      uint32_t s[W];
+      next_succ<W>(it, t, L, v, s);
+      atomicAdd(&hist[(uint32_t)((vec_hash<W>(s) * mul0) >> shift)], 1u);
+    }
+  }
+  __syncthreads();
+  uint32_t mine = 0;
+  for (int q = threadIdx.x; q < P; q += blockDim.x) {
+    pa.hist[(uint64_t)blockIdx.x * P + q] = hist[q];
+    mine += hist[q];
+  }
+  uint32_t total;
+  block_exclusive_scan(mine, total, scan_scratch);
+  if (threadIdx.x == 0) pa.tot[blockIdx.x] = total;
+}
+
+// Pass 2: per slice q (one CTA each), exclusive scan over the batch's CTAs.
+// (A template only so that every translation unit may include this header.)
+template <int Unused>
+__global__ void __launch_bounds__(gx::kBlock) part_scan_kernel(const gx::PartArgs pa) {
+  __shared__ uint32_t scan_scratch[gx::kBlock / 32 + 1];
+  const int q = blockIdx.x;
+  const int P = 1 << pa.logp;
+  uint32_t running = 0;
+  for (int base = pa.b0; base < pa.b1; base += blockDim.x) {
+    const int b = base + threadIdx.x;
+    const uint32_t x = b < pa.b1 ? pa.hist[(uint64_t)b * P + q] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(x, total, scan_scratch);
+    if (b < pa.b1) pa.off[(uint64_t)b * P + q] = running + ex;
+    running += total;
+  }
+  if (threadIdx.x == 0) pa.ptot[q] = running;
+}
+
+// Pass 3: regenerate the successors and write them slice-major; transitions and
+// deadlocks of the batch's frontier states are accounted here.
+template <int W>
+__global__ void __launch_bounds__(gx::kBlock) part_scatter_kernel(const gx::ExpandArgs a, const gx::PartArgs pa) {
+  extern __shared__ __align__(16) uint32_t sm[];
+  const uint64_t* muls;
+  const uint32_t* t = stage_tables(sm, a.muls, 1, a.blob, a.blob_words, a.stage, muls);
+  uint32_t* cur = sm + 2 * kMaxRounds + (a.stage ? a.blob_words : 0);
+  __shared__ uint32_t scan_scratch[gx::kBlock / 32 + 1];
+  const int P = 1 << pa.logp;
+  const int b = pa.b0 + blockIdx.x;
+  // cursor of slice q = (successors of the batch in slices < q) + (of CTAs before b in slice q)
+  uint32_t running = 0;
+  __syncthreads();
+  for (int base = 0; base < P; base += blockDim.x) {
+    const int q = base + threadIdx.x;
+    const uint32_t x = q < P ? pa.ptot[q] : 0u;
+    uint32_t total;
+    const uint32_t ex = block_exclusive_scan(x, total, scan_scratch);
+    if (q < P) cur[q] = running + ex + pa.off[(uint64_t)b * P + q];
+    running += total;
+  }
+  __syncthreads();
+  const NetBlobLayout& L = a.lay;
+  const uint64_t mul0 = muls[0];
+  const int shift = 64 - pa.logp;
+  uint64_t lo, hi;
+  part_range(a, pa, b, lo, hi);
+  unsigned long long trans = 0;
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    uint32_t v[W];
+    load_vec<W>(a.frontier + (i & a.fmask) * W, v);
+    const uint32_t cnt = count_succ<W>(t, L, v);
+    trans += cnt;
+    if (cnt == 0) {
+      const uint64_t h = state_digest<W>(t, L, v);
+      const unsigned long long di = atomicAdd(&a.ctl->dl_count, 1ull);
+      atomicAdd(&a.ctl->dl_sum, (unsigned long long)h);
+      atomicXor(&a.ctl->dl_xor, (unsigned long long)h);
+      if (di < a.dl_cap) store_vec<W>(a.dl_buf + di * W, v);
+    }
+    SuccIter it;
+    it.init();
+    for (uint32_t k = 0; k < cnt; ++k) {
+      uint32_t s[W];
+      next_succ<W>(it, t, L, v, s);
+      const uint32_t q = (uint32_t)((vec_hash<W>(s) * mul0) >> shift);
+      const uint32_t pos = atomicAdd(&cur[q], 1u);
+      store_vec<W>(pa.succ + (uint64_t)pos * W, s);
+    }
+  }
+  trans = warp_sum(trans);
+  if ((threadIdx.x & 31) == 0 && trans) atomicAdd(&a.ctl->transitions, trans);
+}
+
+// Pass 4: find-or-put of the buffered successors in buffer order (slice by slice).
+template <int W, int B, int G>
+__global__ void __launch_bounds__(gx::kBlock) part_probe_kernel(const gx::ExpandArgs a, const uint32_t* succ,
+                                                                uint64_t n) {
+  __shared__ uint64_t muls[kMaxRounds];
+  for (int i = threadIdx.x; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const Group<G> g;
+  uint32_t probes = 0, err = 0;
+  __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
+  WarpStage st{stage_mem[threadIdx.x >> 5], 0};
+  while (true) {
+    unsigned long long chunk = 0;
+    if (lane == 0) chunk = atomicAdd(&a.ctl->claim, 32ull);
+    chunk = __shfl_sync(FULLMASK, chunk, 0);
+    if (chunk >= n) break;
+    const uint64_t idx = chunk + lane;
+    bool has[1] = {idx < n};
+    uint32_t s[1][W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) s[0][w] = 0;
+    if (has[0]) load_vec<W>(succ + idx * W, s[0]);
+    insert_lanes<W, B, G, 1>(a, muls, g, has, s, probes, err, st);
+  }
+  st.flush<W>(a, err);
+  const unsigned long long pr = warp_sum((unsigned long long)probes);
+  err = __reduce_or_sync(FULLMASK, err);
+  if (lane == 0) {
     if (pr) atomicAdd(&a.ctl->probes, pr);
     if (err) atomicOr(&a.ctl->error, err);
   }
@@ -327,11 +619,40 @@ cudaError_t launch_fop(const FopArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int W>
+cudaError_t launch_part_count(const ExpandArgs& a, const PartArgs& p, size_t smem, cudaStream_t st) {
+  gxd::part_count_kernel<W><<<p.nb, kBlock, smem, st>>>(a, p);
+  return cudaGetLastError();
+}
+inline cudaError_t launch_part_scan(const PartArgs& p, cudaStream_t st) {
+  gxd::part_scan_kernel<0><<<1 << p.logp, kBlock, 0, st>>>(p);
+  return cudaGetLastError();
+}
+template <int W>
+cudaError_t launch_part_scatter(const ExpandArgs& a, const PartArgs& p, size_t smem, cudaStream_t st) {
+  gxd::part_scatter_kernel<W><<<p.b1 - p.b0, kBlock, smem, st>>>(a, p);
+  return cudaGetLastError();
+}
+template <int W, int B, int G>
+cudaError_t launch_part_probe(const ExpandArgs& a, const uint32_t* succ, uint64_t n, int grid, cudaStream_t st) {
+  gxd::part_probe_kernel<W, B, G><<<grid, kBlock, 0, st>>>(a, succ, n);
+  return cudaGetLastError();
+}
+
 template <int W, int B, int G>
 const KernelSet* kernel_set() {
-  static const KernelSet ks{&launch_expand<W, B, G>, &launch_init<W, B, G>, &launch_fop<W, B, G>,
+  static const KernelSet ks{&launch_expand<W, B, G>,
+                            &launch_part_count<W>,
+                            &launch_part_scan,
+                            &launch_part_scatter<W>,
+                            &launch_part_probe<W, B, G>,
+                            &launch_init<W, B, G>,
+                            &launch_fop<W, B, G>,
                             reinterpret_cast<const void*>(&gxd::expand_kernel<W, B, G>),
-                            reinterpret_cast<const void*>(&gxd::fop_kernel<W, B, G>)};
+                            reinterpret_cast<const void*>(&gxd::fop_kernel<W, B, G>),
+                            reinterpret_cast<const void*>(&gxd::part_count_kernel<W>),
+                            reinterpret_cast<const void*>(&gxd::part_scatter_kernel<W>),
+                            reinterpret_cast<const void*>(&gxd::part_probe_kernel<W, B, G>)};
   return &ks;
 }
 

@@ -49,6 +49,21 @@ struct ExpandArgs {
   uint32_t dl_cap;
 };
 
+// Partitioned expansion of one level (or one batch of it): successors are
+// counted per table slice, scattered slice-major into a buffer, then probed
+// slice by slice so the probed part of the table stays in L2.
+struct PartArgs {
+  uint32_t* hist;   // [nb * P]: successors of CTA b that fall in slice q, at b * P + q
+  uint32_t* off;    // [nb * P]: exclusive scan over the batch's CTAs, per slice
+  uint32_t* ptot;   // [P]: successors of the batch per slice
+  uint32_t* tot;    // [nb]: successors per CTA
+  uint32_t* succ;   // successor buffer, W words per vector, slice-major
+  int nb;           // CTAs of the count and scatter passes (static frontier ranges)
+  int logp;         // P = 2^logp slices
+  uint64_t range;   // frontier states per CTA
+  int b0, b1;       // CTAs of the current batch
+};
+
 struct InitArgs {
   Muls muls;
   int rounds, log2nb;
@@ -78,10 +93,17 @@ struct FopArgs {
 
 struct KernelSet {
   cudaError_t (*expand)(const ExpandArgs&, int grid, size_t smem, cudaStream_t);
+  cudaError_t (*part_count)(const ExpandArgs&, const PartArgs&, size_t smem, cudaStream_t);
+  cudaError_t (*part_scan)(const PartArgs&, cudaStream_t);
+  cudaError_t (*part_scatter)(const ExpandArgs&, const PartArgs&, size_t smem, cudaStream_t);
+  cudaError_t (*part_probe)(const ExpandArgs&, const uint32_t* succ, uint64_t n, int grid, cudaStream_t);
   cudaError_t (*init)(const InitArgs&, cudaStream_t);
   cudaError_t (*fop)(const FopArgs&, int grid, cudaStream_t);
   const void* expand_fn;  // for occupancy queries and attributes
   const void* fop_fn;
+  const void* part_count_fn;
+  const void* part_scatter_fn;
+  const void* part_probe_fn;
 };
 
 // Kernels for slot width W, bucket words B and group lanes G; nullptr if the

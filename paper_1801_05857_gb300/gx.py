@@ -52,7 +52,8 @@ class gx_explore_opts(ctypes.Structure):
     _fields_ = [("bucket_words", u32), ("group_lanes", u32), ("hash_rounds", u32),
                 ("stop_at_first_deadlock", u32), ("max_levels", u32), ("deadlock_cap", u32),
                 ("ctas_per_sm", u32), ("reserved0", u32), ("table_bytes", u64),
-                ("frontier_states", u64)]
+                ("frontier_states", u64), ("successor_buffer", u64), ("slice_log2", u32),
+                ("partition_min_states", u32)]
 
 
 class gx_stats_t(ctypes.Structure):
@@ -63,7 +64,7 @@ class gx_stats_t(ctypes.Structure):
                 ("group_lanes", u32), ("hash_rounds", u32), ("complete", u32), ("status", u32),
                 ("reserved", u32), ("fill", ctypes.c_double), ("gpu_ms", ctypes.c_double),
                 ("expand_ms", ctypes.c_double), ("expand_launches", u64), ("probes", u64),
-                ("h2d_bytes", u64), ("d2h_bytes", u64)]
+                ("h2d_bytes", u64), ("d2h_bytes", u64), ("partitioned_levels", u64)]
 
 
 _lib = None

@@ -200,3 +200,28 @@ def test_mid_config_against_stored_oracle(cuda, bucket):
         g["deadlock_count"], g["deadlock_sum"], g["deadlock_xor"])
     assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])
     assert s["fill"] <= 0.75
+
+
+def _part_nets():
+    return [inputs.token_ring(11),
+            inputs.random_network(0, 13, 64, 1, 3, 16, n_sync=8, parties=3, cluster=4),
+            inputs.random_network(7, 6, 8, 1, 3, 8, n_sync=2, parties=2),
+            inputs.random_network(6, 8, 8, 0, 2, 10, n_sync=4, parties=2)]
+
+
+@pytest.mark.parametrize("net", _part_nets(), ids=lambda n: n.name)
+@pytest.mark.parametrize("slices,buf", [(1, 0), (3, 40000), (6, 0), (4, 20000)])
+def test_partitioned_path(cuda, net, slices, buf):
+    """Every level through the count / scatter / slice-ordered probe passes; a small
+    successor buffer splits levels into several batches."""
+    s = assert_parity(net, table_bytes=1 << 25, slice_log2=slices, successor_buffer=buf,
+                      partition_min_states=1)
+    assert s["partitioned_levels"] > 0
+
+
+def test_partitioned_buffer_too_small_falls_back(cuda):
+    """A level whose CTA ranges produce more successors than the buffer holds is
+    expanded by the direct kernel instead; results stay exact."""
+    s = assert_parity(inputs.token_ring(10), table_bytes=1 << 22, slice_log2=2, successor_buffer=1,
+                      partition_min_states=1)
+    assert s["partitioned_levels"] < s["n_levels"] - 1  # only levels with one successor fit
