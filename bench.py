@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-table", action="store_true", help="skip the Sec. 5.1 find-or-put part")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
     ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
                          "exploration for every (bucket, group) size; one JSON line per point")
@@ -220,6 +221,53 @@ def table_point(torch, gx, keys, n, dup, words, table_words, bucket, group, roun
             "frac_random_gather32": round((n / (ms * 1e-3)) / gather32, 4) if gather32 else None}
 
 
+def batched_part(torch, gx, inputs, steps: int = 5) -> dict:
+    """The 256-network batched workload: one graph launch (autotuned) vs one gx_explore
+    per network in sequence.  Tables of 2^21 slots per network (at most 46 % full)."""
+    nets = inputs.batch_workload()
+    handles = [gx.load_network(n) for n in nets]
+    b = gx.batch_create(handles)
+    o = gx.batch_opts(hash_rounds=32, table_slots=1 << 21)
+    ws = gx.batch_alloc_workspace(b, o)
+    tune_ms = gx.batch_autotune(b, o, ws)
+    gx.batch_explore(b, o, ws)
+    ts = []
+    for _ in range(steps):
+        gx.batch_explore(b, o, ws)
+        ts.append(gx.batch_stats(b, 0)["gpu_ms"])
+    ts.sort()
+    states = sum(gx.batch_stats(b, i)["states"] for i in range(len(nets)))
+    trans = sum(gx.batch_stats(b, i)["transitions"] for i in range(len(nets)))
+    del ws
+    torch.cuda.empty_cache()
+    # sequential: one gx_explore per network, same table size and options
+    wss = {}
+    for h in handles:  # one workspace per slot width, sized for the largest network tables
+        w = gx.layout(h)["vector_words"]
+        o2 = gx.default_opts(bucket_words=max(o.bucket_words, w), group_lanes=o.group_lanes,
+                             hash_rounds=32, table_bytes=(1 << 21) * 4 * w)
+        need = gx.workspace_bytes(h, o2)
+        if w not in wss or wss[w][1] < need:
+            wss[w] = (o2, need)
+    wss = {w: (o2, torch.empty(need, dtype=torch.uint8, device="cuda")) for w, (o2, need) in wss.items()}
+    seq_states = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h in handles:
+        o2, wsw = wss[gx.layout(h)["vector_words"]]
+        gx.explore(h, o2, wsw)
+        seq_states += gx.stats(h)["states"]
+    torch.cuda.synchronize()
+    seq = time.perf_counter() - t0
+    med = ts[len(ts) // 2]
+    return {"networks": len(nets), "states": states, "transitions": trans,
+            "autotuned": {"bucket_words": o.bucket_words, "group_lanes": o.group_lanes,
+                          "chunk_states": o.chunk_states, "tune_best_ms": round(tune_ms, 3)},
+            "ms": round(med, 3), "states_per_s": round(states / (med * 1e-3), 1),
+            "sequential_ms": round(seq * 1e3, 3), "sequential_states_per_s": round(seq_states / seq, 1),
+            "speedup_vs_sequential": round(seq * 1e3 / med, 2)}
+
+
 def cpu_baseline(net, sample: int) -> dict:
     import oracle
     r = oracle.explore(net, max_explored=sample)
@@ -337,6 +385,10 @@ def run_ours(args, world, rank, local, pg):
             del keys
         table_part = {"keys": n, "key_words": 1, "table_words": 1 << 27, "points": pts}
 
+    batch_part = None
+    if rank == 0 and not args.no_batch:
+        batch_part = batched_part(torch, gx, inputs)
+
     # end to end through the public API with host-resident inputs: load the network
     # description from host arrays, explore with a library-allocated workspace, read the
     # results back to the host
@@ -380,6 +432,7 @@ def run_ours(args, world, rank, local, pg):
             "transitions_per_s": round(tps, 1),
             "roofline": roof,
             "find_or_put": table_part,
+            "batched": batch_part,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps * (1 + launches // args.steps),

@@ -206,6 +206,60 @@ gx_status gx_set_digest(gx_net* net, void* workspace, uint64_t workspace_bytes, 
                         uint64_t* count, uint64_t* sum, uint64_t* xr);
 
 /* ------------------------------------------------------------------------------------------
+ * Batched exploration of many independent networks (no counterpart in the
+ * paper, which explores one network per run; each network is explored exactly
+ * as by gx_explore).  All networks advance one BFS level per iteration inside
+ * one persistent kernel launch; the iterations run on the device as a CUDA
+ * graph with a conditional WHILE node, so one graph launch explores the whole
+ * batch.  Narrower vectors are padded to the batch's widest slot.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct gx_batch gx_batch;
+
+typedef struct gx_batch_opts {
+  uint32_t bucket_words;    /* 4, 8, 16 or 32; 0 = 8 */
+  uint32_t group_lanes;     /* 1, 2 or 4 (see gx_batch_autotune for the built pairs); 0 = 1 */
+  uint32_t hash_rounds;     /* 1..64; 0 = 8 */
+  uint32_t chunk_states;    /* frontier states a warp claims at a time, a multiple of 32
+                               up to 4096; 0 = 32 */
+  uint64_t table_slots;     /* per-network table slots when expected_states is NULL
+                               (rounded up to a power of two); 0 = 2^20 */
+  const uint64_t* expected_states; /* optional host array, one entry per network: network i
+                               gets a table of at least expected_states[i] / 0.75 slots */
+  uint32_t levels_cap;      /* BFS levels kept per network; 0 = 4096 */
+  uint32_t reserved;
+} gx_batch_opts;
+
+/* Make a batch from encoded networks (their encodings are copied; the
+ * networks may be freed afterwards).  Host-only. */
+gx_status gx_batch_create(const gx_net* const* nets, uint32_t n, gx_batch** out);
+void gx_batch_free(gx_batch* batch);
+
+/* Device workspace bytes for gx_batch_explore with these options. */
+gx_status gx_batch_workspace_bytes(const gx_batch* batch, const gx_batch_opts* opts, uint64_t* bytes);
+
+/* Explore every network of the batch (one graph launch).  workspace: device
+ * pointer, 256-byte aligned, at least gx_batch_workspace_bytes bytes (required).
+ * The instantiated graph is cached in the batch for the same workspace and
+ * options.  Per-network results via gx_batch_stats / gx_batch_levels; the first
+ * failing network's error is returned (the others' results stay valid).
+ * Synchronises `stream`. */
+gx_status gx_batch_explore(gx_batch* batch, const gx_batch_opts* opts, void* workspace,
+                           uint64_t workspace_bytes, void* stream);
+
+/* Results of network i in the last gx_batch_explore (gpu_ms is the whole batch). */
+gx_status gx_batch_stats(const gx_batch* batch, uint32_t i, gx_stats_t* out);
+gx_status gx_batch_levels(const gx_batch* batch, uint32_t i, uint64_t* out, uint32_t cap,
+                          uint32_t* n_levels);
+
+/* Autotuner: times the whole batch for every built (bucket_words, group_lanes)
+ * pair -- (4,1) (8,1) (8,2) (16,1) (16,2) (32,2) (32,4), those not narrower than
+ * the slots -- and chunk_states 32, 64, 128 (median of three runs each, CUDA
+ * events), then writes the fastest into *opts (other fields kept) and its time
+ * into *best_ms.  The workspace must fit every candidate (all need the same). */
+gx_status gx_batch_autotune(gx_batch* batch, gx_batch_opts* opts, void* workspace,
+                            uint64_t workspace_bytes, void* stream, double* best_ms);
+
+/* ------------------------------------------------------------------------------------------
  * Exploration that allocates nothing.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory -- a host
  * framework that has reserved the GPU's memory for its own pool (cudaMalloc

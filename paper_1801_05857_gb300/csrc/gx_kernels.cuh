@@ -167,6 +167,21 @@ __device__ __forceinline__ const uint32_t* stage_tables(uint32_t* sm, const gx::
   return s_tab;
 }
 
+// Where find-or-put inserts and where new vectors go: one network's table and
+// frontier ring (the level being expanded starts at cur_begin).
+struct Target {
+  uint32_t* table;
+  int log2nb, rounds;
+  unsigned long long* next_end;
+  uint32_t* frontier;
+  uint64_t fmask;
+  uint64_t cur_begin;
+};
+
+__device__ __forceinline__ Target target_of(const gx::ExpandArgs& a) {
+  return Target{a.table, a.log2nb, a.rounds, &a.ctl->next_end, a.frontier, a.fmask, a.cur_begin};
+}
+
 // Per-warp staging of new vectors in shared memory: lanes that inserted a
 // vector append it here (ballot + popc, no atomic); every 32 staged vectors
 // are written to the next level with one global atomicAdd and one coalesced
@@ -178,10 +193,10 @@ struct WarpStage {
   int n;          // staged vectors (uniform in the warp)
 
   template <int W>
-  __device__ __forceinline__ void write_out(const gx::ExpandArgs& a, int m, uint32_t& err) {
+  __device__ __forceinline__ void write_out(const Target& a, int m, uint32_t& err) {
     const int lane = threadIdx.x & 31;
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&a.ctl->next_end, (unsigned long long)m);
+    if (lane == 0) base = atomicAdd(a.next_end, (unsigned long long)m);
     base = __shfl_sync(FULLMASK, base, 0);
     if (lane < m) {
       const uint64_t pos = base + lane;
@@ -194,7 +209,7 @@ struct WarpStage {
   }
 
   template <int W>
-  __device__ __forceinline__ void push(const gx::ExpandArgs& a, bool ins, const uint32_t (&v)[W],
+  __device__ __forceinline__ void push(const Target& a, bool ins, const uint32_t (&v)[W],
                                        uint32_t& err) {
     const int lane = threadIdx.x & 31;
     const uint32_t im = __ballot_sync(FULLMASK, ins);
@@ -219,7 +234,7 @@ struct WarpStage {
   }
 
   template <int W>
-  __device__ __forceinline__ void flush(const gx::ExpandArgs& a, uint32_t& err) {
+  __device__ __forceinline__ void flush(const Target& a, uint32_t& err) {
     __syncwarp();
     if (n > 0) write_out<W>(a, n, err);
     n = 0;
@@ -243,7 +258,7 @@ struct PerLane {
 // inserted go to the warp's staging buffer.
 // Must be called by all 32 lanes of the warp together.
 template <int W, int B, int G, int K>
-__device__ __forceinline__ void insert_lanes(const gx::ExpandArgs& a, const uint64_t* muls,
+__device__ __forceinline__ void insert_lanes(const Target& a, const uint64_t* muls,
                                              const Group<G>& g, const bool (&has)[K],
                                              const uint32_t (&s)[K][W], uint32_t& probes,
                                              uint32_t& err, WarpStage& st) {
@@ -285,8 +300,13 @@ __device__ __forceinline__ void insert_lanes(const gx::ExpandArgs& a, const uint
   for (int k = 0; k < K; ++k) st.push<W>(a, inserted[k], s[k], err);
 }
 
+// Resident CTAs per SM the level kernel is compiled for (register budget).
+#ifndef GX_EXPAND_MIN_CTAS
+#define GX_EXPAND_MIN_CTAS 5
+#endif
+
 template <int W, int B, int G>
-__global__ void __launch_bounds__(gx::kBlock) expand_kernel(const gx::ExpandArgs a) {
+__global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(const gx::ExpandArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   const uint64_t* muls;
   const uint32_t* t = stage_tables(sm, a.muls, a.rounds, a.blob, a.blob_words, a.stage, muls);
@@ -298,6 +318,7 @@ __global__ void __launch_bounds__(gx::kBlock) expand_kernel(const gx::ExpandArgs
   uint32_t probes = 0, err = 0;
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
+  const Target tg = target_of(a);
 
   while (true) {
     unsigned long long chunk = 0;
@@ -337,10 +358,10 @@ __global__ void __launch_bounds__(gx::kBlock) expand_kernel(const gx::ExpandArgs
           for (int w = 0; w < W; ++w) s[k][w] = 0;
         }
       }
-      insert_lanes<W, B, G, K>(a, muls, g, has, s, probes, err, st);
+      insert_lanes<W, B, G, K>(tg, muls, g, has, s, probes, err, st);
     }
   }
-  st.flush<W>(a, err);
+  st.flush<W>(tg, err);
   trans = warp_sum(trans);
   const unsigned long long pr = warp_sum((unsigned long long)probes);
   err = __reduce_or_sync(FULLMASK, err);
@@ -517,6 +538,7 @@ __global__ void __launch_bounds__(gx::kBlock) part_probe_kernel(const gx::Expand
   uint32_t probes = 0, err = 0;
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
+  const Target tg = target_of(a);
   while (true) {
     unsigned long long chunk = 0;
     if (lane == 0) chunk = atomicAdd(&a.ctl->claim, 32ull);
@@ -528,9 +550,9 @@ __global__ void __launch_bounds__(gx::kBlock) part_probe_kernel(const gx::Expand
 #pragma unroll
     for (int w = 0; w < W; ++w) s[0][w] = 0;
     if (has[0]) load_vec<W>(succ + idx * W, s[0]);
-    insert_lanes<W, B, G, 1>(a, muls, g, has, s, probes, err, st);
+    insert_lanes<W, B, G, 1>(tg, muls, g, has, s, probes, err, st);
   }
-  st.flush<W>(a, err);
+  st.flush<W>(tg, err);
   const unsigned long long pr = warp_sum((unsigned long long)probes);
   err = __reduce_or_sync(FULLMASK, err);
   if (lane == 0) {

@@ -67,6 +67,12 @@ class gx_stats_t(ctypes.Structure):
                 ("h2d_bytes", u64), ("d2h_bytes", u64), ("partitioned_levels", u64)]
 
 
+class gx_batch_opts(ctypes.Structure):
+    _fields_ = [("bucket_words", u32), ("group_lanes", u32), ("hash_rounds", u32),
+                ("chunk_states", u32), ("table_slots", u64), ("expected_states", P(u64)),
+                ("levels_cap", u32), ("reserved", u32)]
+
+
 _lib = None
 
 
@@ -105,6 +111,13 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "gx_probe_random": ([u32, vp, u64, u64, u32, u64, vp, vp], ctypes.c_int),
         "gx_explore_noalloc": ([vp, P(gx_explore_opts), vp, P(gx_stats_t), P(u64), u32, P(u32)],
                                ctypes.c_int),
+        "gx_batch_create": ([P(vp), u32, P(vp)], ctypes.c_int),
+        "gx_batch_free": ([vp], None),
+        "gx_batch_workspace_bytes": ([vp, P(gx_batch_opts), P(u64)], ctypes.c_int),
+        "gx_batch_explore": ([vp, P(gx_batch_opts), vp, u64, vp], ctypes.c_int),
+        "gx_batch_stats": ([vp, u32, P(gx_stats_t)], ctypes.c_int),
+        "gx_batch_levels": ([vp, u32, P(u64), u32, P(u32)], ctypes.c_int),
+        "gx_batch_autotune": ([vp, P(gx_batch_opts), vp, u64, vp, P(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -284,6 +297,83 @@ def explore_noalloc(net: Net, opts: gx_explore_opts | None = None, stream=None,
                                     levels_cap, ctypes.byref(n)))
     stats_d = {name: getattr(s, name) for name, _ in gx_stats_t._fields_ if name != "reserved"}
     return stats_d, [int(x) for x in lv[:min(int(n.value), levels_cap)]]
+
+
+# --------------------------------------------------------------------------------------------
+# batched exploration
+# --------------------------------------------------------------------------------------------
+
+class Batch:
+    """Owner of a gx_batch handle (gx_batch_free on deletion)."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = handle
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.gx_batch_free(self.handle)
+            self.handle = None
+
+
+def batch_create(nets) -> Batch:
+    """gx_batch_create from a list of Net handles (or inputs.Network objects)."""
+    handles = [n if isinstance(n, Net) else load_network(n) for n in nets]
+    arr = (ctypes.c_void_p * len(handles))(*[h.handle for h in handles])
+    h = ctypes.c_void_p()
+    _check(lib().gx_batch_create(arr, len(handles), ctypes.byref(h)))
+    return Batch(h.value, len(handles))
+
+
+def batch_opts(expected_states=None, **kw) -> gx_batch_opts:
+    o = gx_batch_opts()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, int(v))
+    if expected_states is not None:
+        arr = np.ascontiguousarray(expected_states, dtype=np.uint64)
+        o._keep = arr
+        o.expected_states = arr.ctypes.data_as(P(u64))
+    return o
+
+
+def batch_workspace_bytes(b: Batch, opts: gx_batch_opts | None = None) -> int:
+    n = u64()
+    _check(lib().gx_batch_workspace_bytes(b.handle, ctypes.byref(opts) if opts else None, ctypes.byref(n)))
+    return int(n.value)
+
+
+def batch_alloc_workspace(b: Batch, opts: gx_batch_opts | None = None, device="cuda"):
+    import torch
+    return torch.empty(batch_workspace_bytes(b, opts), dtype=torch.uint8, device=device)
+
+
+def batch_explore(b: Batch, opts: gx_batch_opts | None, workspace, stream=None) -> None:
+    _check(lib().gx_batch_explore(b.handle, ctypes.byref(opts) if opts else None, _ptr(workspace),
+                                  workspace.numel(), _stream(stream)))
+
+
+def batch_stats(b: Batch, i: int) -> dict:
+    s = gx_stats_t()
+    _check(lib().gx_batch_stats(b.handle, i, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in gx_stats_t._fields_ if name != "reserved"}
+
+
+def batch_levels(b: Batch, i: int) -> list:
+    n = u32()
+    _check(lib().gx_batch_levels(b.handle, i, None, 0, ctypes.byref(n)))
+    out = np.zeros(max(int(n.value), 1), dtype=np.uint64)
+    _check(lib().gx_batch_levels(b.handle, i, out.ctypes.data_as(P(u64)), int(n.value), ctypes.byref(n)))
+    return [int(x) for x in out[:int(n.value)]]
+
+
+def batch_autotune(b: Batch, opts: gx_batch_opts, workspace, stream=None) -> float:
+    """gx_batch_autotune: updates opts in place, returns the best batch time (ms)."""
+    ms = ctypes.c_double()
+    _check(lib().gx_batch_autotune(b.handle, ctypes.byref(opts), _ptr(workspace), workspace.numel(),
+                                   _stream(stream), ctypes.byref(ms)))
+    return float(ms.value)
 
 
 # --------------------------------------------------------------------------------------------

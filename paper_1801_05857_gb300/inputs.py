@@ -260,6 +260,47 @@ def workload(name: str) -> Network:
     return random_network(**WORKLOADS[name])
 
 
+def batch_params(seed: int) -> dict:
+    """Generator arguments of one network of the batched workload: 4-10 processes
+    x 8-32 local states, out-degree 1-3, about half the processes in two-party
+    rules, local edges in blocks of 4-8 states."""
+    r = substream(seed, 77)
+    n = r.between(4, 10)
+    ns = r.between(8, 32)
+    cl = r.between(4, 8)
+    nl = 2 * n + r.between(0, 4)
+    nsync = max(1, min(nl - 1, n // 2 + 1 + r.between(0, 3)))
+    return dict(seed=1000 + seed, n_procs=n, n_states=ns, deg_lo=1, deg_hi=3, n_labels=nl,
+                n_sync=nsync, parties=2, cluster=cl, name=f"batch_{seed}")
+
+
+# Seeds of batch_params whose networks have 10^3..10^6 reachable states, chosen by
+# tests/golden/make_golden.py (it runs the oracle on candidate seeds in order and keeps
+# those in range); the batched workload is the first 256 of them.
+BATCH_SEEDS = [
+    0, 1, 2, 3, 4, 6, 7, 8, 11, 13, 15, 19, 21, 22, 23, 24,
+    28, 29, 30, 31, 32, 33, 35, 36, 37, 38, 42, 44, 45, 47, 48, 49,
+    51, 52, 53, 54, 55, 56, 58, 60, 61, 63, 66, 67, 69, 70, 71, 72,
+    73, 74, 75, 76, 79, 80, 82, 83, 84, 85, 87, 88, 89, 90, 91, 92,
+    94, 97, 100, 101, 102, 103, 104, 105, 110, 111, 112, 113, 114, 116, 117, 118,
+    120, 126, 127, 128, 129, 130, 131, 134, 136, 137, 138, 139, 140, 141, 142, 144,
+    149, 150, 151, 152, 155, 156, 157, 159, 160, 161, 162, 164, 165, 166, 169, 170,
+    171, 173, 174, 176, 178, 180, 181, 182, 185, 186, 189, 191, 192, 193, 194, 197,
+    198, 200, 201, 202, 205, 207, 208, 210, 211, 213, 214, 215, 216, 217, 219, 220,
+    221, 224, 228, 230, 232, 234, 235, 238, 239, 240, 241, 243, 244, 247, 248, 249,
+    250, 251, 252, 253, 254, 255, 256, 257, 260, 264, 265, 267, 268, 271, 272, 273,
+    276, 279, 282, 283, 284, 285, 286, 289, 290, 291, 292, 294, 296, 297, 298, 299,
+    300, 301, 303, 304, 305, 306, 307, 312, 313, 315, 316, 317, 318, 320, 321, 322,
+    325, 327, 328, 329, 330, 331, 332, 333, 335, 336, 337, 338, 339, 340, 343, 344,
+    345, 347, 349, 350, 351, 352, 353, 355, 356, 357, 358, 359, 361, 362, 363, 365,
+    366, 367, 369, 371, 373, 374, 376, 377, 379, 380, 381, 382, 383, 384, 387, 389,
+]
+
+
+def batch_workload(count: int = 256) -> list:
+    return [random_network(**batch_params(s)) for s in BATCH_SEEDS[:count]]
+
+
 # --------------------------------------------------------------------------------------------
 # Key sequences for the isolated hash-table experiment (Sec. 5.1)
 # --------------------------------------------------------------------------------------------

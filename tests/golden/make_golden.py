@@ -35,7 +35,30 @@ def write(name: str, gen: dict) -> None:
     print(name, r.states, r.transitions, len(r.levels), round(r.seconds, 1), "s")
 
 
+def write_batch(count: int = 256, lo: int = 1_000, hi: int = 1_000_000) -> None:
+    """Select the batched workload: candidate seeds of inputs.batch_params in order, kept
+    when the oracle finds lo..hi reachable states; store every kept network's results."""
+    kept = []
+    seed = 0
+    while len(kept) < count:
+        gen = inputs.batch_params(seed)
+        r = oracle.explore(inputs.random_network(**gen), max_explored=hi + 1, deadlocks_cap=16)
+        if r.complete and lo <= r.states <= hi:
+            kept.append(dict(batch_seed=seed, generator=gen, states=r.states, transitions=r.transitions,
+                             levels=r.levels, deadlock_count=r.deadlock_count,
+                             deadlock_sum=r.deadlock_sum, deadlock_xor=r.deadlock_xor,
+                             set_sum=r.set_sum, set_xor=r.set_xor))
+            print(len(kept), seed, r.states, flush=True)
+        seed += 1
+    with open(os.path.join(HERE, "batch_networks.json"), "w") as f:
+        json.dump(dict(note="written by tests/golden/make_golden.py batch from oracle.explore",
+                       seeds=[k["batch_seed"] for k in kept], networks=kept), f)
+    print("BATCH_SEEDS =", [k["batch_seed"] for k in kept])
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["mid"]
     if "mid" in which:
         write("mid_network.json", MID)
+    if "batch" in which:
+        write_batch()
