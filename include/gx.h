@@ -112,7 +112,7 @@ typedef struct gx_explore_opts {
   uint32_t max_levels;     /* stop after this many levels have been expanded; 0 = no limit */
   uint32_t deadlock_cap;   /* deadlock states kept for gx_deadlocks; 0 = 1024 */
   uint32_t ctas_per_sm;    /* persistent CTAs per SM; 0 = as many as fit */
-  uint32_t reserved0;
+  uint32_t guided_batch;   /* GX_DL_GUIDED: open states expanded per iteration; 0 = 8192 */
   uint64_t table_bytes;    /* hash-table size; rounded down to a power-of-two number of
                               buckets.  0 = 1 GiB */
   uint64_t frontier_states;/* capacity of the frontier ring in vectors; rounded up to a
@@ -127,6 +127,9 @@ typedef struct gx_explore_opts {
                                     at most 4096 slices) */
   uint32_t partition_min_states; /* levels with at least this many states are partitioned;
                                     0 = never (default) */
+  uint32_t guided_bins;          /* GX_DL_GUIDED: priority bins; 0 = 32 */
+  float guided_scale;            /* GX_DL_GUIDED: score at which a state falls in the last
+                                    bin (scores are predicted distances / max_dist); 0 = 1.0 */
 } gx_explore_opts;
 
 /* Fill *opts with the defaults described above. */
@@ -153,8 +156,12 @@ gx_status gx_explore(gx_net* net, const gx_explore_opts* opts, void* workspace,
  *     first deadlock (every deadlock of that level is reported);
  *   mode GX_DL_BFS_ALL: full exploration, every deadlock reported;
  *   mode GX_DL_GUIDED: best-first order by the scoring network set with
- *     gx_guided_set_weights, falling back to exhaustive search; absence of
- *     deadlocks is reported only after the whole state space was explored.
+ *     gx_guided_set_weights: each iteration expands the guided_batch open
+ *     states of the best non-empty priority bin (last in, first out), scoring
+ *     every new state as it is found.  Every state is pushed and eventually
+ *     expanded, so the search is exhaustive: it stops at the first deadlock
+ *     (reported with its path, gx_guided_trace) and reports absence only after
+ *     the whole state space was explored.  Workspace: gx_guided_workspace_bytes.
  * out_states: host pointer receiving up to cap deadlock states, n_procs
  * local states each (uint32); *n_found gets the total number found (may
  * exceed cap).  Other arguments as for gx_explore. */
@@ -204,6 +211,71 @@ gx_status gx_deadlocks(const gx_net* net, uint32_t* out, uint32_t cap, uint32_t*
  * ones of the last search (the table is read in place). */
 gx_status gx_set_digest(gx_net* net, void* workspace, uint64_t workspace_bytes, void* stream,
                         uint64_t* count, uint64_t* sum, uint64_t* xr);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned guidance for deadlock search (no counterpart in the paper; the
+ * exhaustive search it reorders is the one of Sec. 3).
+ *
+ * Scoring network: x = hist / 16 where hist[i] = number of processes whose
+ * local state is i (the one-hot local states summed over processes; networks
+ * used with it have at most 16 local states per process), then
+ * h1 = relu(W1 x + b1) (128 x 16), h2 = relu(W2 h1 + b2) (128 x 128),
+ * y = w3 . h2 + b3, trained to predict distance-to-deadlock / max_dist.  The
+ * parameters are one FP32 vector W1 | b1 | W2 | b2 | w3 | b3 (GX_MLP_PARAMS
+ * floats, device memory); every kernel uses the weights rounded to BF16
+ * (round to nearest even) and accumulates in FP32.
+ * ---------------------------------------------------------------------------------------- */
+#define GX_MLP_IN 16
+#define GX_MLP_HIDDEN 128
+#define GX_MLP_PARAMS (GX_MLP_HIDDEN * GX_MLP_IN + GX_MLP_HIDDEN + GX_MLP_HIDDEN * GX_MLP_HIDDEN + \
+                       GX_MLP_HIDDEN + GX_MLP_HIDDEN + 1)
+/* Device bytes of the optimiser state gx_mlp_train needs for a batch size. */
+#define GX_MLP_STATE_BYTES(batch) (4ull * (3ull * GX_MLP_PARAMS + 2ull) + 8ull * (batch))
+
+/* Training examples from the last gx_explore on `net` (same workspace): every
+ * state found gets its distance to the nearest deadlock (backward
+ * breadth-first search over the explored graph, run as level-by-level
+ * relaxation on the device: a state is at distance r when one of its
+ * successors is at r - 1).  Writes up to cap examples: hist_out (device,
+ * 16 uint8 per example) and label_out (device, float: min(distance, max_dist)
+ * / max_dist, 1.0 when no deadlock is reachable).  dist_scratch: device, one
+ * uint32 per table slot (gx_stats table_slots).  *n_out = states found (may
+ * exceed cap).  GX_ERR_INVALID if a process has more than 16 local states. */
+gx_status gx_training_set(gx_net* net, void* workspace, uint64_t workspace_bytes, void* stream,
+                          uint32_t* dist_scratch, uint32_t max_dist, uint8_t* hist_out,
+                          float* label_out, uint64_t cap, uint64_t* n_out);
+
+/* Seeded initialisation of params (device, GX_MLP_PARAMS floats): weights
+ * uniform in +-1/sqrt(fan_in) from a splitmix64 stream, biases 0. */
+gx_status gx_mlp_init(float* params, uint64_t seed, void* stream);
+
+/* Scores of n examples (hist: device, 16 uint8 each) into out (device, n floats). */
+gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, float* out, void* stream);
+
+/* Gradient of the mean squared error over n examples at params (grad: device,
+ * GX_MLP_PARAMS floats; loss: device, one float). */
+gx_status gx_mlp_grad(const float* params, const uint8_t* hist, const float* label, uint64_t n,
+                      float* grad, float* loss, void* stream);
+
+/* `steps` Adam steps (lr, beta 0.9 / 0.999) on mini-batches of `batch`
+ * examples drawn by a counter-based stream from `seed`.  state: device,
+ * GX_MLP_STATE_BYTES(batch) bytes (overwritten); loss: device, one float per
+ * step (the mini-batch loss).  Synchronises `stream`. */
+gx_status gx_mlp_train(float* params, float* state, const uint8_t* hist, const float* label, uint64_t n,
+                       uint32_t batch, uint32_t steps, float lr, uint64_t seed, float* loss, void* stream);
+
+/* Scoring weights for GX_DL_GUIDED searches on `net`: a device pointer to
+ * GX_MLP_PARAMS floats that must stay valid while such searches run. */
+gx_status gx_guided_set_weights(gx_net* net, const float* params);
+
+/* Workspace bytes for a GX_DL_GUIDED search (table, priority bins, the log of
+ * expanded states with their parents). */
+gx_status gx_guided_workspace_bytes(const gx_net* net, const gx_explore_opts* opts, uint64_t* bytes);
+
+/* The path of the deadlock found by the last GX_DL_GUIDED search: up to cap
+ * states (n_procs local states each, host memory), from the initial state to
+ * the deadlock; *len gets the path length in states. */
+gx_status gx_guided_trace(const gx_net* net, uint32_t* out, uint32_t cap, uint32_t* len);
 
 /* ------------------------------------------------------------------------------------------
  * Batched exploration of many independent networks (no counterpart in the

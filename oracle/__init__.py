@@ -10,6 +10,7 @@ computes and which passages of the paper it follows):
 * ``deadlock_distances`` -- backward-BFS distance of every reachable state to a deadlock
 * ``product_matrix`` -- brute force: the product's transition-count matrix as a
   sum of Kronecker products, and BFS levels by matrix-vector steps (tiny networks)
+* ``mlp``          -- FP64 forward and gradient of the guided search's scoring network
 """
 from __future__ import annotations
 

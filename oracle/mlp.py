@@ -1,0 +1,78 @@
+"""FP64 reference of the scoring network of the guided search -- TEST INFRASTRUCTURE ONLY.
+
+The network (no counterpart in the paper): x = hist / 16, h1 = relu(W1 x + b1),
+h2 = relu(W2 h1 + b2), y = w3 . h2 + b3, loss = mean (y - label)^2, with the
+parameter vector laid out W1 (128 x 16) | b1 | W2 (128 x 128) | b2 | w3 | b3.
+With bf16=True the weights W1, W2, w3 are first rounded to bfloat16 (the
+upper 16 bits of the IEEE binary32 pattern, round to nearest, ties to even),
+as the GPU does; everything else is float64.  Gradients are taken with respect
+to the unrounded parameters through the rounded weights (the rounding itself
+passes gradients unchanged), which is what an optimiser on FP32 master
+weights sees.
+"""
+import numpy as np
+
+IN, H = 16, 128
+NPARAM = H * IN + H + H * H + H + H + 1
+
+
+def bf16_round(a) -> np.ndarray:
+    """float32 values rounded to the nearest bfloat16 (ties to even), as float32."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (b >> np.uint64(16)) & np.uint64(1)
+    r = ((b + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    return (r & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32)
+
+
+def unpack(p):
+    p = np.asarray(p, dtype=np.float32)
+    o = 0
+    W1 = p[o:o + H * IN].reshape(H, IN); o += H * IN
+    b1 = p[o:o + H]; o += H
+    W2 = p[o:o + H * H].reshape(H, H); o += H * H
+    b2 = p[o:o + H]; o += H
+    w3 = p[o:o + H]; o += H
+    b3 = p[o]
+    return W1, b1, W2, b2, w3, b3
+
+
+def _weights(p, bf16):
+    W1, b1, W2, b2, w3, b3 = unpack(p)
+    if bf16:
+        W1, W2, w3 = bf16_round(W1), bf16_round(W2), bf16_round(w3)
+    f = lambda a: np.asarray(a, dtype=np.float64)
+    return f(W1), f(b1), f(W2), f(b2), f(w3), float(b3)
+
+
+def forward(p, hist, bf16=True):
+    W1, b1, W2, b2, w3, b3 = _weights(p, bf16)
+    x = np.asarray(hist, dtype=np.float64) / 16.0
+    a1 = x @ W1.T + b1
+    z1 = np.maximum(a1, 0)
+    a2 = z1 @ W2.T + b2
+    z2 = np.maximum(a2, 0)
+    return z2 @ w3 + b3
+
+
+def loss_and_grad(p, hist, label, bf16=True):
+    W1, b1, W2, b2, w3, b3 = _weights(p, bf16)
+    x = np.asarray(hist, dtype=np.float64) / 16.0
+    t = np.asarray(label, dtype=np.float64)
+    n = len(t)
+    a1 = x @ W1.T + b1
+    z1 = np.maximum(a1, 0)
+    a2 = z1 @ W2.T + b2
+    z2 = np.maximum(a2, 0)
+    y = z2 @ w3 + b3
+    loss = np.mean((y - t) ** 2)
+    dy = 2.0 * (y - t) / n
+    gw3 = z2.T @ dy
+    gb3 = dy.sum()
+    d2 = np.outer(dy, w3) * (a2 > 0)
+    gW2 = d2.T @ z1
+    gb2 = d2.sum(axis=0)
+    d1 = (d2 @ W2) * (a1 > 0)
+    gW1 = d1.T @ x
+    gb1 = d1.sum(axis=0)
+    g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gw3, [gb3]])
+    return loss, g

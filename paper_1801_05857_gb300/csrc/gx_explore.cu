@@ -505,7 +505,7 @@ gx_status gx_find_deadlocks(gx_net* h, const gx_explore_opts* opts, uint32_t mod
   if (mode == GX_DL_BFS_FIRST || mode == GX_DL_BFS_ALL) {
     s = gx::run_search(h, opts, mode == GX_DL_BFS_FIRST, ws, ws_bytes, static_cast<cudaStream_t>(stream));
   } else if (mode == GX_DL_GUIDED) {
-    return gx::fail(GX_ERR_INVALID, "guided mode needs scoring weights (not set)");
+    s = gx::run_guided(h, opts, ws, ws_bytes, static_cast<cudaStream_t>(stream));
   } else {
     return gx::fail(GX_ERR_INVALID, "unknown deadlock-search mode");
   }

@@ -1,0 +1,781 @@
+// Learned guidance for deadlock search (no counterpart in the paper; the
+// search it reorders is the exploration of Sec. 3 with on-the-fly deadlock
+// detection, and every state still goes through the find-or-put of Sec. 4.1).
+//
+// Training examples (gx_training_set): after a gx_explore, every state in the
+// table gets its distance to the nearest deadlock by level-by-level
+// relaxation -- distance 0 for states without successors, distance r for a
+// state with a successor at distance r - 1 -- looking successors up in the
+// same table.  Then each state becomes one example: the histogram of its
+// processes' local states and the capped, normalised distance.
+//
+// Guided search (gx_find_deadlocks, GX_DL_GUIDED): open states live in
+// priority bins (stacks) by score; each iteration one CTA pops up to
+// guided_batch states from the best non-empty bin, then a persistent kernel
+// expands them: it logs each (state, parent log index), detects deadlocks,
+// find-or-puts every successor and scores each new one with the MLP (warp-
+// cooperative, BF16 weights in shared memory, FP32 accumulation) before
+// pushing it to its bin.  Every state is pushed once and popped once, so the
+// search ends either at a deadlock or after the whole state space.
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "gx_kernels.cuh"
+
+namespace gx {
+
+struct GuidedCtl {
+  unsigned long long found;      // smallest log index of a deadlock found, ~0 if none
+  unsigned long long batch_n;    // states popped for the current iteration
+  unsigned long long log_base;   // log index of the first popped state
+  unsigned long long log_count;  // states logged (expanded) so far
+  unsigned long long inserted;   // states inserted into the table
+  unsigned long long transitions;
+  unsigned long long probes;
+  unsigned int error, done;
+  unsigned long long dl_count;
+  unsigned long long claim;
+};
+
+struct GuidedArgs {
+  const uint32_t* blob;
+  NetBlobLayout lay;
+  uint32_t blob_words;
+  int stage;
+  Muls muls;
+  int rounds, log2nb;
+  uint32_t* table;
+  GuidedCtl* ctl;
+  unsigned long long* bin_count;  // [nbins]
+  uint32_t* bins;                 // [nbins][bin_cap] entries of E words
+  uint64_t bin_cap;
+  int nbins;
+  float scale;
+  uint32_t* batch;                // [batch_cap] entries
+  uint32_t batch_cap;
+  uint32_t* log;                  // [log_cap] entries
+  uint64_t log_cap;
+  const float* params;            // MLP, FP32 (rounded to BF16 when staged)
+  uint32_t init_vec[4];
+};
+
+constexpr unsigned int ERR_BINS = 16u, ERR_LOG = 32u, ERR_WIDE = 64u;
+
+}  // namespace gx
+
+namespace gxd {
+
+using gx::GuidedArgs;
+using gx::GuidedCtl;
+
+constexpr int MH = GX_MLP_HIDDEN;
+constexpr int MI = GX_MLP_IN;
+constexpr int LD1 = MI + 1;  // padded rows in shared memory (no bank conflicts)
+constexpr int LD2 = MH + 1;
+
+// Slot index of v in the table, or -1 when v is not stored.  Slots of a
+// bucket fill in order and are never freed, so an empty slot ends the search.
+template <int W, int B>
+__device__ __forceinline__ int64_t find_slot(const uint32_t* __restrict__ table, int log2nb, int rounds,
+                                             const uint64_t* __restrict__ muls, const uint32_t (&v)[W]) {
+  constexpr int S = B / W;
+  const uint64_t h = vec_hash<W>(v);
+  for (int k = 0; k < rounds; ++k) {
+    const uint64_t b = bucket_of(h, muls[k], log2nb);
+    uint32_t s[B];
+    load_words<B>(table + b * (uint64_t)B, s);
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      bool eq = true, empty = true;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        eq &= s[j * W + w] == v[w];
+        empty &= s[j * W + w] == 0u;
+      }
+      if (eq) return (int64_t)(b * S + j);
+      if (empty) return -1;
+    }
+  }
+  return -1;
+}
+
+template <int W>
+__device__ __forceinline__ bool slot_vec(const uint32_t* table, uint64_t i, uint32_t (&v)[W]) {
+  load_vec<W>(table + i * W, v);
+  bool tagged = true;
+#pragma unroll
+  for (int w = 0; w < W; ++w) tagged &= (v[w] & kTag) != 0;
+  return tagged;
+}
+
+// Histogram of local-state indices (each < 16, else *bad is set), 4 per word.
+template <int W>
+__device__ __forceinline__ void local_hist(const uint32_t* t, const NetBlobLayout& L, const uint32_t (&v)[W],
+                                           uint32_t (&hw)[4], uint32_t& bad) {
+  hw[0] = hw[1] = hw[2] = hw[3] = 0;
+  for (uint32_t p = 0; p < L.n_procs; ++p) {
+    const uint32_t s = local_state<W>(t, L, v, p);
+    if (s >= 16) {
+      bad = 1;
+      continue;
+    }
+    const uint32_t inc = 1u << ((s & 3) * 8);
+    if ((s >> 2) == 0) hw[0] += inc;
+    else if ((s >> 2) == 1) hw[1] += inc;
+    else if ((s >> 2) == 2) hw[2] += inc;
+    else hw[3] += inc;
+  }
+}
+
+constexpr uint32_t INF = 0xFFFFFFFFu;
+
+template <int W>
+__global__ void __launch_bounds__(gx::kBlock) label_init_kernel(const uint32_t* table, uint64_t slots, const uint32_t* t,
+                                                                NetBlobLayout L, uint32_t* dist) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
+    uint32_t v[W];
+    if (!slot_vec<W>(table, i, v)) {
+      dist[i] = INF;
+      continue;
+    }
+    dist[i] = count_succ<W>(t, L, v) == 0 ? 0u : INF;
+  }
+}
+
+template <int W, int B>
+__global__ void __launch_bounds__(gx::kBlock) label_sweep_kernel(const uint32_t* table, uint64_t slots,
+                                                                 const uint32_t* t, NetBlobLayout L, gx::Muls mm,
+                                                                 int rounds, int log2nb, uint32_t* dist, uint32_t r,
+                                                                 unsigned long long* changed) {
+  __shared__ uint64_t muls[kMaxRounds];
+  for (int i = threadIdx.x; i < rounds; i += blockDim.x) muls[i] = mm.m[i];
+  __syncthreads();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t any = 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
+    if (dist[i] != INF) continue;
+    uint32_t v[W];
+    if (!slot_vec<W>(table, i, v)) continue;
+    const uint32_t cnt = count_succ<W>(t, L, v);
+    SuccIter it;
+    it.init();
+    for (uint32_t k = 0; k < cnt; ++k) {
+      uint32_t s[W];
+      next_succ<W>(it, t, L, v, s);
+      const int64_t j = find_slot<W, B>(table, log2nb, rounds, muls, s);
+      if (j >= 0 && dist[j] == r - 1) {
+        dist[i] = r;
+        any = 1;
+        break;
+      }
+    }
+  }
+  if (__any_sync(FULLMASK, any != 0) && (threadIdx.x & 31) == 0) atomicAdd(changed, 1ull);
+}
+
+template <int W>
+__global__ void __launch_bounds__(gx::kBlock) label_gather_kernel(const uint32_t* table, uint64_t slots,
+                                                                  const uint32_t* t, NetBlobLayout L,
+                                                                  const uint32_t* dist, uint32_t max_dist,
+                                                                  uint8_t* hist_out, float* label_out, uint64_t cap,
+                                                                  unsigned long long* count,
+                                                                  unsigned long long* bad_flag) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += stride) {
+    uint32_t v[W];
+    if (!slot_vec<W>(table, i, v)) continue;
+    uint32_t hw[4], bad = 0;
+    local_hist<W>(t, L, v, hw, bad);
+    if (bad) atomicOr(bad_flag, 1ull);
+    const unsigned long long pos = atomicAdd(count, 1ull);
+    if (pos >= cap) continue;
+    uint32_t* dst = reinterpret_cast<uint32_t*>(hist_out + pos * 16);
+    dst[0] = hw[0];
+    dst[1] = hw[1];
+    dst[2] = hw[2];
+    dst[3] = hw[3];
+    const uint32_t d = dist[i] == INF ? max_dist : min(dist[i], max_dist);
+    label_out[pos] = (float)d / (float)max_dist;
+  }
+}
+
+// ---- guided search
+
+// MLP weights staged in shared memory (BF16-rounded, held as FP32).
+struct MlpSmem {
+  float* W1;  // [MH][LD1]
+  float* b1;  // [MH]
+  float* W2;  // [MH][LD2]
+  float* b2;  // [MH]
+  float* w3;  // [MH]
+  float b3;
+};
+
+__device__ __forceinline__ float bf16r(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
+
+__device__ __forceinline__ MlpSmem stage_mlp(float* sm, const float* p) {
+  MlpSmem m;
+  m.W1 = sm;
+  m.b1 = m.W1 + MH * LD1;
+  m.W2 = m.b1 + MH;
+  m.b2 = m.W2 + MH * LD2;
+  m.w3 = m.b2 + MH;
+  const float* pW1 = p;
+  const float* pb1 = pW1 + MH * MI;
+  const float* pW2 = pb1 + MH;
+  const float* pb2 = pW2 + MH * MH;
+  const float* pw3 = pb2 + MH;
+  for (int i = threadIdx.x; i < MH * MI; i += blockDim.x) m.W1[(i / MI) * LD1 + i % MI] = bf16r(pW1[i]);
+  for (int i = threadIdx.x; i < MH * MH; i += blockDim.x) m.W2[(i / MH) * LD2 + i % MH] = bf16r(pW2[i]);
+  for (int i = threadIdx.x; i < MH; i += blockDim.x) {
+    m.b1[i] = pb1[i];
+    m.b2[i] = pb2[i];
+    m.w3[i] = bf16r(pw3[i]);
+  }
+  m.b3 = pw3[MH];
+  return m;
+}
+
+constexpr size_t kMlpSmemFloats = MH * LD1 + MH + MH * LD2 + MH + MH;
+
+// Score of the state whose histogram words hw (identical in all lanes) are
+// given; all 32 lanes cooperate (lane owns hidden units lane + 32q).
+__device__ __forceinline__ float warp_score(const MlpSmem& m, const uint32_t (&hw)[4], float* h1) {
+  const int lane = threadIdx.x & 31;
+  float x[MI];
+#pragma unroll
+  for (int i = 0; i < MI; ++i) x[i] = (float)((hw[i >> 2] >> ((i & 3) * 8)) & 0xFFu) * (1.0f / 16.0f);
+  float a1[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = lane + 32 * q;
+    float a = m.b1[k];
+#pragma unroll
+    for (int i = 0; i < MI; ++i) a += m.W1[k * LD1 + i] * x[i];
+    a1[q] = fmaxf(a, 0.f);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) h1[lane + 32 * q] = a1[q];
+  __syncwarp();
+  float part = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int k = lane + 32 * q;
+    float a = m.b2[k];
+    for (int j = 0; j < MH; ++j) a += m.W2[k * LD2 + j] * h1[j];
+    part += m.w3[k] * fmaxf(a, 0.f);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULLMASK, part, o);
+  return part + m.b3;
+}
+
+template <int W>
+__device__ __forceinline__ void push_bin(const GuidedArgs& a, float score, const uint32_t (&v)[W], uint32_t parent,
+                                         uint32_t& err) {
+  constexpr int E = W + 1;
+  int b = (int)(score / a.scale * (float)a.nbins);
+  b = b < 0 ? 0 : (b >= a.nbins ? a.nbins - 1 : b);
+  for (; b < a.nbins; ++b) {  // a full bin spills into the next (worse) one
+    const unsigned long long pos = atomicAdd(&a.bin_count[b], 1ull);
+    if (pos < a.bin_cap) {
+      uint32_t* e = a.bins + ((uint64_t)b * a.bin_cap + pos) * E;
+#pragma unroll
+      for (int w = 0; w < W; ++w) e[w] = v[w];
+      e[W] = parent;
+      return;
+    }
+  }
+  err |= gx::ERR_BINS;
+}
+
+template <int W, int B>
+__global__ void __launch_bounds__(gx::kBlock) guided_init_kernel(const GuidedArgs a) {
+  extern __shared__ __align__(16) float gsm[];
+  __shared__ uint64_t muls[kMaxRounds];
+  __shared__ float h1buf[MH];
+  for (int i = threadIdx.x; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
+  const MlpSmem m = stage_mlp(gsm, a.params);
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  uint32_t v[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) v[w] = a.init_vec[w];
+  uint32_t hw[4], bad = 0;
+  local_hist<W>(a.blob, a.lay, v, hw, bad);
+  const float y = warp_score(m, hw, h1buf);
+  if (threadIdx.x != 0) return;
+  const Group<1> g;
+  uint32_t probes = 0, err = bad ? gx::ERR_WIDE : 0u;
+  const int r = find_or_put<W, B, 1>(a.table, a.log2nb, a.rounds, muls, v, g, probes);
+  if (r != FOP_INSERTED) err |= gx::ERR_TABLE_FULL;
+  else {
+    a.ctl->inserted = 1;
+    push_bin<W>(a, y, v, 0xFFFFFFFFu, err);
+  }
+  if (err) atomicOr(&a.ctl->error, err);
+}
+
+// One CTA: pop the next batch from the best non-empty bin.
+template <int W>
+__global__ void __launch_bounds__(1024) guided_select_kernel(const GuidedArgs a) {
+  constexpr int E = W + 1;
+  __shared__ int best;
+  __shared__ unsigned long long take, top;
+  if (threadIdx.x == 0) {
+    best = -1;
+    GuidedCtl& c = *a.ctl;
+    c.batch_n = 0;
+    c.claim = 0;
+    if (c.found == ~0ull && !c.error) {
+      for (int b = 0; b < a.nbins; ++b) {
+        unsigned long long cnt = a.bin_count[b];
+        if (cnt > a.bin_cap) cnt = a.bin_cap;  // failed pushes left the counter past the end
+        a.bin_count[b] = cnt;
+        if (cnt > 0) {
+          best = b;
+          break;
+        }
+      }
+      if (best < 0) {
+        c.done = 1;
+      } else {
+        const unsigned long long cnt = a.bin_count[best];
+        take = cnt < a.batch_cap ? cnt : a.batch_cap;
+        top = cnt - take;
+        if (c.log_count + take > a.log_cap) {
+          c.error |= gx::ERR_LOG;
+          best = -1;
+        } else {
+          a.bin_count[best] = top;
+          c.batch_n = take;
+          c.log_base = c.log_count;
+          c.log_count += take;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (best < 0) return;
+  const uint32_t* src = a.bins + ((uint64_t)best * a.bin_cap + top) * E;
+  for (uint64_t i = threadIdx.x; i < take * E; i += blockDim.x) a.batch[i] = src[i];
+}
+
+template <int W, int B>
+__global__ void __launch_bounds__(gx::kBlock) guided_expand_kernel(const GuidedArgs a) {
+  constexpr int E = W + 1;
+  extern __shared__ __align__(16) float gsm[];
+  __shared__ uint64_t muls[kMaxRounds];
+  __shared__ float h1buf[gx::kBlock / 32][MH];
+  for (int i = threadIdx.x; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
+  const MlpSmem m = stage_mlp(gsm, a.params);
+  const uint32_t* t = a.blob;
+  if (a.stage) {
+    uint32_t* s_tab = reinterpret_cast<uint32_t*>(gsm + kMlpSmemFloats);
+    for (uint32_t i = threadIdx.x; i < a.blob_words; i += blockDim.x) s_tab[i] = a.blob[i];
+    t = s_tab;
+  }
+  __syncthreads();
+  const NetBlobLayout& L = a.lay;
+  const int lane = threadIdx.x & 31;
+  float* h1 = h1buf[threadIdx.x >> 5];
+  const Group<1> g;
+  const unsigned long long n = a.ctl->batch_n;
+  const unsigned long long log_base = a.ctl->log_base;
+  unsigned long long trans = 0, ins = 0;
+  uint32_t probes = 0, err = 0;
+  while (true) {
+    unsigned long long chunk = 0;
+    if (lane == 0) chunk = atomicAdd(&a.ctl->claim, 32ull);
+    chunk = __shfl_sync(FULLMASK, chunk, 0);
+    if (chunk >= n) break;
+    const unsigned long long idx = chunk + lane;
+    const bool valid = idx < n;
+    uint32_t v[W];
+    uint32_t parent = 0;
+#pragma unroll
+    for (int w = 0; w < W; ++w) v[w] = 0;
+    const unsigned long long li = log_base + idx;
+    if (valid) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) v[w] = a.batch[idx * E + w];
+      parent = a.batch[idx * E + W];
+      uint32_t* le = a.log + li * E;
+#pragma unroll
+      for (int w = 0; w < W; ++w) le[w] = v[w];
+      le[W] = parent;
+    }
+    uint32_t remaining = valid ? count_succ<W>(t, L, v) : 0u;
+    trans += remaining;
+    if (valid && remaining == 0) {
+      atomicMin(&a.ctl->found, li);
+      atomicAdd(&a.ctl->dl_count, 1ull);
+    }
+    SuccIter it;
+    it.init();
+    while (__any_sync(FULLMASK, remaining != 0)) {
+      uint32_t s[W];
+      const bool has = remaining != 0;
+      if (has) {
+        next_succ<W>(it, t, L, v, s);
+        --remaining;
+      }
+      bool inserted = false;
+      if (has) {
+        const int r = find_or_put<W, B, 1>(a.table, a.log2nb, a.rounds, muls, s, g, probes);
+        if (r == FOP_FULL) err |= gx::ERR_TABLE_FULL;
+        inserted = r == FOP_INSERTED;
+      }
+      uint32_t hw[4] = {0, 0, 0, 0}, bad = 0;
+      if (inserted) local_hist<W>(t, L, s, hw, bad);
+      if (bad) err |= gx::ERR_WIDE;
+      uint32_t im = __ballot_sync(FULLMASK, inserted);
+      ins += inserted ? 1u : 0u;
+      while (im) {  // score the new states one at a time, all lanes together
+        const int src = __ffs(im) - 1;
+        im &= im - 1;
+        uint32_t h[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h[q] = __shfl_sync(FULLMASK, hw[q], src);
+        const float y = warp_score(m, h, h1);
+        if (lane == src) push_bin<W>(a, y, s, (uint32_t)li, err);
+      }
+    }
+  }
+  trans = warp_sum(trans);
+  ins = warp_sum(ins);
+  const unsigned long long pr = warp_sum((unsigned long long)probes);
+  err = __reduce_or_sync(FULLMASK, err);
+  if (lane == 0) {
+    if (trans) atomicAdd(&a.ctl->transitions, trans);
+    if (ins) atomicAdd(&a.ctl->inserted, ins);
+    if (pr) atomicAdd(&a.ctl->probes, pr);
+    if (err) atomicOr(&a.ctl->error, err);
+  }
+}
+
+}  // namespace gxd
+
+namespace gx {
+namespace {
+
+#define GG_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return gx::fail(GX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+inline uint64_t a256(uint64_t x) { return (x + 255) & ~255ull; }
+
+struct GKernels {
+  void (*sweep)(const uint32_t*, uint64_t, const uint32_t*, NetBlobLayout, Muls, int, int, uint32_t*, uint32_t,
+                unsigned long long*);
+  const void* init;
+  const void* select;
+  const void* expand;
+};
+
+template <int W, int B>
+GKernels gk() {
+  return GKernels{&gxd::label_sweep_kernel<W, B>, reinterpret_cast<const void*>(&gxd::guided_init_kernel<W, B>),
+                  reinterpret_cast<const void*>(&gxd::guided_select_kernel<W>),
+                  reinterpret_cast<const void*>(&gxd::guided_expand_kernel<W, B>)};
+}
+
+bool gk_lookup(int W, int B, GKernels& k) {
+#define GX_GK(w, b) \
+  if (W == w && B == b) { k = gk<w, b>(); return true; }
+  GX_GK(1, 4) GX_GK(1, 8) GX_GK(1, 16) GX_GK(1, 32)
+  GX_GK(2, 4) GX_GK(2, 8) GX_GK(2, 16) GX_GK(2, 32)
+  GX_GK(4, 4) GX_GK(4, 8) GX_GK(4, 16) GX_GK(4, 32)
+#undef GX_GK
+  return false;
+}
+
+int log2_of(uint64_t x) {
+  int l = 0;
+  while ((1ull << l) < x) ++l;
+  return l;
+}
+
+struct GPlan {
+  int W, B, rounds, nbins;
+  float scale;
+  uint32_t batch_cap;
+  uint64_t nb, slots, bin_cap, log_cap;
+  uint64_t off_ctl, off_blob, off_bincnt, off_table, off_bins, off_batch, off_log, total;
+  GKernels k;
+};
+
+gx_status guided_plan(const Net& net, const gx_explore_opts* o, GPlan& P) {
+  gx_explore_opts d;
+  gx_default_opts(&d);
+  if (!o) o = &d;
+  P.W = (int)net.slot_words;
+  P.B = o->bucket_words ? (int)o->bucket_words : 8;
+  if (P.B < P.W || !gk_lookup(P.W, P.B, P.k)) return fail(GX_ERR_INVALID, "unsupported bucket_words for guided search");
+  P.rounds = o->hash_rounds ? (int)o->hash_rounds : 8;
+  if (P.rounds < 1 || P.rounds > kMaxRounds) return fail(GX_ERR_INVALID, "hash_rounds must be 1..64");
+  P.nbins = o->guided_bins ? (int)o->guided_bins : 32;
+  if (P.nbins < 1 || P.nbins > 1024) return fail(GX_ERR_INVALID, "guided_bins must be 1..1024");
+  P.scale = o->guided_scale > 0.f ? o->guided_scale : 1.0f;
+  P.batch_cap = o->guided_batch ? o->guided_batch : 8192;
+  const uint64_t table_bytes = o->table_bytes ? o->table_bytes : (1ull << 30);
+  uint64_t nb = 1;
+  while (nb * 2 * 4ull * P.B <= table_bytes) nb *= 2;
+  if (nb < 2) return fail(GX_ERR_INVALID, "table_bytes is smaller than two buckets");
+  P.nb = nb;
+  P.slots = nb * (uint64_t)(P.B / P.W);
+  P.log_cap = P.slots;                                   // every state is expanded at most once
+  P.bin_cap = std::max<uint64_t>(P.batch_cap, P.slots / 4);
+  const uint64_t E = (uint64_t)P.W + 1;
+  uint64_t off = 0;
+  P.off_ctl = off;
+  off = a256(off + sizeof(GuidedCtl));
+  P.off_blob = off;
+  off = a256(off + 4ull * net.blob.size());
+  P.off_bincnt = off;
+  off = a256(off + 8ull * P.nbins);
+  P.off_table = off;
+  off = a256(off + 4ull * P.B * P.nb);
+  P.off_bins = off;
+  off = a256(off + 4ull * E * P.bin_cap * P.nbins);
+  P.off_batch = off;
+  off = a256(off + 4ull * E * P.batch_cap);
+  P.off_log = off;
+  off = a256(off + 4ull * E * P.log_cap);
+  P.total = off;
+  return GX_OK;
+}
+
+}  // namespace
+
+gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t ws_bytes, cudaStream_t st) {
+  const Net& net = h->net;
+  if (!h->guided_params) return fail(GX_ERR_INVALID, "guided mode needs scoring weights (gx_guided_set_weights)");
+  for (uint32_t p = 0; p < net.n_procs; ++p)
+    if (net.n_states[p] > 16) return fail(GX_ERR_INVALID, "guided mode needs at most 16 local states per process");
+  GPlan P;
+  gx_status s = guided_plan(net, opts, P);
+  if (s != GX_OK) return s;
+  if (!ws) return fail(GX_ERR_INVALID, "guided search needs a workspace (gx_guided_workspace_bytes)");
+  if (ws_bytes < P.total)
+    return fail(GX_ERR_OOM, "workspace holds " + std::to_string(ws_bytes) + " bytes, need " + std::to_string(P.total));
+  int dev = 0, sms = 0, optin = 0;
+  GG_CUDA(cudaGetDevice(&dev));
+  GG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  char* base = static_cast<char*>(ws);
+  GuidedCtl* ctl = reinterpret_cast<GuidedCtl*>(base + P.off_ctl);
+  GuidedArgs a{};
+  a.blob = reinterpret_cast<const uint32_t*>(base + P.off_blob);
+  a.lay = net.lay;
+  a.blob_words = (uint32_t)net.blob.size();
+  hash_multipliers(a.muls.m, kMaxRounds);
+  a.rounds = P.rounds;
+  a.log2nb = log2_of(P.nb);
+  a.table = reinterpret_cast<uint32_t*>(base + P.off_table);
+  a.ctl = ctl;
+  a.bin_count = reinterpret_cast<unsigned long long*>(base + P.off_bincnt);
+  a.bins = reinterpret_cast<uint32_t*>(base + P.off_bins);
+  a.bin_cap = P.bin_cap;
+  a.nbins = P.nbins;
+  a.scale = P.scale;
+  a.batch = reinterpret_cast<uint32_t*>(base + P.off_batch);
+  a.batch_cap = P.batch_cap;
+  a.log = reinterpret_cast<uint32_t*>(base + P.off_log);
+  a.log_cap = P.log_cap;
+  a.params = h->guided_params;
+  for (int w = 0; w < 4; ++w) a.init_vec[w] = net.init_vec[w];
+  const size_t mlp_bytes = sizeof(float) * gxd::kMlpSmemFloats;
+  const size_t blob_bytes = 4ull * net.blob.size();
+  a.stage = (mlp_bytes + blob_bytes <= (size_t)optin - 32 * 1024) ? 1 : 0;
+  const size_t smem = mlp_bytes + (a.stage ? blob_bytes : 0);
+  GG_CUDA(cudaFuncSetAttribute(P.k.expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GG_CUDA(cudaFuncSetAttribute(P.k.init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_bytes));
+  int per_sm = 0;
+  GG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.k.expand, kBlock, smem));
+  const int grid = sms * std::max(per_sm, 1);
+
+  cudaEvent_t e0, e1;
+  GG_CUDA(cudaEventCreate(&e0));
+  GG_CUDA(cudaEventCreate(&e1));
+  GG_CUDA(cudaEventRecord(e0, st));
+  GG_CUDA(cudaMemcpyAsync(base + P.off_blob, net.blob.data(), blob_bytes, cudaMemcpyHostToDevice, st));
+  GuidedCtl init{};
+  init.found = ~0ull;
+  GG_CUDA(cudaMemcpyAsync(ctl, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+  GG_CUDA(cudaMemsetAsync(a.bin_count, 0, 8ull * P.nbins, st));
+  GG_CUDA(cudaMemsetAsync(a.table, 0, 4ull * P.B * P.nb, st));
+  void* args[] = {&a};
+  GG_CUDA(cudaLaunchKernel(P.k.init, dim3(1), dim3(kBlock), args, mlp_bytes, st));
+  GuidedCtl hc{};
+  uint64_t iters = 0;
+  while (true) {
+    GG_CUDA(cudaLaunchKernel(P.k.select, dim3(1), dim3(1024), args, 0, st));
+    GG_CUDA(cudaLaunchKernel(P.k.expand, dim3(grid), dim3(kBlock), args, smem, st));
+    GG_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    ++iters;
+    if (hc.found != ~0ull || hc.done || hc.error) break;
+  }
+  GG_CUDA(cudaEventRecord(e1, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+
+  // the path of the deadlock: follow parent log indices back to the initial state
+  h->guided_trace.clear();
+  h->deadlocks.clear();
+  const int E = P.W + 1;
+  if (hc.found != ~0ull) {
+    std::vector<std::vector<uint32_t>> path;
+    uint64_t li = hc.found;
+    while (true) {
+      uint32_t e[5] = {0, 0, 0, 0, 0};
+      GG_CUDA(cudaMemcpy(e, a.log + li * E, 4ull * E, cudaMemcpyDeviceToHost));
+      uint32_t w4[4] = {0, 0, 0, 0};
+      for (int w = 0; w < P.W; ++w) w4[w] = e[w];
+      std::vector<uint32_t> local(net.n_procs);
+      unpack_host(net, w4, local.data());
+      path.push_back(local);
+      if (e[P.W] == 0xFFFFFFFFu || path.size() > P.log_cap) break;
+      li = e[P.W];
+    }
+    std::reverse(path.begin(), path.end());
+    for (const auto& st2 : path) h->guided_trace.insert(h->guided_trace.end(), st2.begin(), st2.end());
+    h->deadlocks = path.back();
+  }
+  gx_stats_t& S = h->stats;
+  std::memset(&S, 0, sizeof(S));
+  S.states = hc.inserted;
+  S.explored = hc.log_count;
+  S.transitions = hc.transitions;
+  S.deadlock_count = hc.found != ~0ull ? 1 : 0;
+  S.first_deadlock_level = hc.found != ~0ull ? (int64_t)(h->guided_trace.size() / net.n_procs) - 1 : -1;
+  S.table_slots = P.slots;
+  S.vector_words = net.vector_words;
+  S.slot_words = (uint32_t)P.W;
+  S.bucket_words = (uint32_t)P.B;
+  S.group_lanes = 1;
+  S.hash_rounds = (uint32_t)P.rounds;
+  S.complete = hc.done ? 1u : 0u;
+  S.fill = (double)hc.inserted / (double)P.slots;
+  S.gpu_ms = ms;
+  S.expand_launches = iters;
+  S.probes = hc.probes;
+  h->levels.clear();
+  h->have_result = true;
+  gx_status rs = GX_OK;
+  if (hc.error & ERR_TABLE_FULL) rs = fail(GX_ERR_TABLE_FULL, "hash table full during guided search");
+  else if (hc.error & ERR_BINS) rs = fail(GX_ERR_FRONTIER_OVERFLOW, "priority bins full");
+  else if (hc.error & ERR_LOG) rs = fail(GX_ERR_OOM, "log of expanded states full");
+  else if (hc.error & ERR_WIDE) rs = fail(GX_ERR_INVALID, "a local state index is 16 or more");
+  S.status = (uint32_t)rs;
+  return rs;
+}
+
+}  // namespace gx
+
+extern "C" {
+
+gx_status gx_guided_set_weights(gx_net* h, const float* params) {
+  gx::clear_error();
+  if (!h) return gx::fail(GX_ERR_INVALID, "net is NULL");
+  h->guided_params = params;
+  return GX_OK;
+}
+
+gx_status gx_guided_workspace_bytes(const gx_net* h, const gx_explore_opts* opts, uint64_t* bytes) {
+  gx::clear_error();
+  if (!h || !bytes) return gx::fail(GX_ERR_INVALID, "net or bytes is NULL");
+  gx::GPlan P;
+  gx_status s = gx::guided_plan(h->net, opts, P);
+  if (s != GX_OK) return s;
+  *bytes = P.total;
+  return GX_OK;
+}
+
+gx_status gx_guided_trace(const gx_net* h, uint32_t* out, uint32_t cap, uint32_t* len) {
+  gx::clear_error();
+  if (!h) return gx::fail(GX_ERR_INVALID, "net is NULL");
+  const uint32_t n = h->net.n_procs;
+  const uint32_t states = (uint32_t)(h->guided_trace.size() / n);
+  if (cap && !out) return gx::fail(GX_ERR_INVALID, "out is NULL");
+  const uint32_t k = std::min(states, cap);
+  if (k) std::memcpy(out, h->guided_trace.data(), 4ull * n * k);
+  if (len) *len = states;
+  return GX_OK;
+}
+
+gx_status gx_training_set(gx_net* h, void* ws, uint64_t ws_bytes, void* stream, uint32_t* dist,
+                          uint32_t max_dist, uint8_t* hist_out, float* label_out, uint64_t cap, uint64_t* n_out) {
+  gx::clear_error();
+  if (!h || !ws || !dist) return gx::fail(GX_ERR_INVALID, "net, workspace or dist_scratch is NULL");
+  if (!h->have_result || h->levels.empty()) return gx::fail(GX_ERR_STATE, "run gx_explore on this network first");
+  if (ws_bytes && ws_bytes < h->ws_total) return gx::fail(GX_ERR_INVALID, "workspace smaller than the last search's");
+  if (max_dist == 0) return gx::fail(GX_ERR_INVALID, "max_dist must be positive");
+  if (cap && (!hist_out || !label_out)) return gx::fail(GX_ERR_INVALID, "output arrays are NULL");
+  const gx_stats_t& S = h->stats;
+  gx::GKernels k;
+  if (!gx::gk_lookup((int)S.slot_words, (int)S.bucket_words, k))
+    return gx::fail(GX_ERR_INVALID, "no labelling kernel for this table layout");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  const uint32_t* table = reinterpret_cast<const uint32_t*>(base + h->ws_off_table);
+  const uint32_t* blob = reinterpret_cast<const uint32_t*>(base + h->ws_off_blob);
+  gx::Ctl* ctl = reinterpret_cast<gx::Ctl*>(base + h->ws_off_ctl);
+  unsigned long long* flags = ctl->digest;  // [0] changed, [1] count, [2] bad
+  const uint64_t slots = S.table_slots;
+  const int W = (int)S.slot_words;
+  gx::Muls mm;
+  gx::hash_multipliers(mm.m, gx::kMaxRounds);
+  const int log2nb = gx::log2_of(slots * W / S.bucket_words);
+  int dev = 0, sms = 0;
+  GG_CUDA(cudaGetDevice(&dev));
+  GG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = sms * 8;
+  if (W == 1) gxd::label_init_kernel<1><<<grid, gx::kBlock, 0, st>>>(table, slots, blob, h->net.lay, dist);
+  else if (W == 2) gxd::label_init_kernel<2><<<grid, gx::kBlock, 0, st>>>(table, slots, blob, h->net.lay, dist);
+  else gxd::label_init_kernel<4><<<grid, gx::kBlock, 0, st>>>(table, slots, blob, h->net.lay, dist);
+  GG_CUDA(cudaGetLastError());
+  for (uint32_t r = 1; r <= max_dist; ++r) {
+    GG_CUDA(cudaMemsetAsync(flags, 0, 8, st));
+    k.sweep<<<grid, gx::kBlock, 0, st>>>(table, slots, blob, h->net.lay, mm, (int)S.hash_rounds, log2nb, dist, r,
+                                         flags);
+    GG_CUDA(cudaGetLastError());
+    unsigned long long changed = 0;
+    GG_CUDA(cudaMemcpyAsync(&changed, flags, 8, cudaMemcpyDeviceToHost, st));
+    GG_CUDA(cudaStreamSynchronize(st));
+    if (!changed) break;
+  }
+  GG_CUDA(cudaMemsetAsync(flags + 1, 0, 16, st));
+  if (W == 1)
+    gxd::label_gather_kernel<1><<<grid, gx::kBlock, 0, st>>>(table, slots, blob, h->net.lay, dist, max_dist, hist_out,
+                                                              label_out, cap, flags + 1, flags + 2);
+  else if (W == 2)
+    gxd::label_gather_kernel<2><<<grid, gx::kBlock, 0, st>>>(table, slots, blob, h->net.lay, dist, max_dist, hist_out,
+                                                              label_out, cap, flags + 1, flags + 2);
+  else
+    gxd::label_gather_kernel<4><<<grid, gx::kBlock, 0, st>>>(table, slots, blob, h->net.lay, dist, max_dist, hist_out,
+                                                              label_out, cap, flags + 1, flags + 2);
+  GG_CUDA(cudaGetLastError());
+  unsigned long long res[2] = {0, 0};
+  GG_CUDA(cudaMemcpyAsync(res, flags + 1, 16, cudaMemcpyDeviceToHost, st));
+  GG_CUDA(cudaStreamSynchronize(st));
+  if (n_out) *n_out = res[0];
+  if (res[1]) return gx::fail(GX_ERR_INVALID, "a process has a local state index of 16 or more");
+  return GX_OK;
+}
+
+}  // extern "C"

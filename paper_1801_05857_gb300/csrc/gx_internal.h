@@ -56,8 +56,11 @@ struct gx_net {
   gx_stats_t stats{};
   std::vector<uint64_t> levels;
   std::vector<uint32_t> deadlocks;  // unpacked, n_procs per state
-  // workspace regions of the last search (for gx_set_digest)
+  // workspace regions of the last search (for gx_set_digest, gx_training_set)
   uint64_t ws_off_ctl = 0, ws_off_blob = 0, ws_off_table = 0, ws_total = 0;
+  // guided search: scoring weights (device, caller-owned) and the last deadlock's path
+  const float* guided_params = nullptr;
+  std::vector<uint32_t> guided_trace;
 };
 
 namespace gx {

@@ -123,4 +123,7 @@ cudaError_t launch_digest(int W, const DigestArgs& a, int grid, cudaStream_t st)
 // Hash-constant multipliers: odd 64-bit values drawn from splitmix64.
 void hash_multipliers(uint64_t* out, int n);
 
+// GX_DL_GUIDED search (gx_guided.cu).
+gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t ws_bytes, cudaStream_t st);
+
 }  // namespace gx

@@ -1,0 +1,275 @@
+// The scoring network of the guided deadlock search (no counterpart in the
+// paper): a small MLP that predicts a state's distance to the nearest deadlock
+// from the histogram of its processes' local states.
+//
+//   x  = hist / 16                      (hist[i] = processes in local state i, i < 16)
+//   h1 = relu(W1 x + b1)                W1: 128 x 16
+//   h2 = relu(W2 h1 + b2)               W2: 128 x 128
+//   y  = w3 . h2 + b3
+//
+// The one-hot local state of each process, summed over processes, is the
+// input: the first layer's weights are shared by all processes, which is
+// what lets a network trained on small instances score states of larger ones.
+// Weights are used in BF16 (rounded to nearest even from FP32 master copies
+// that the optimiser updates); every product is accumulated in FP32.
+//
+// Parameter vector (FP32, GX_MLP_PARAMS floats): W1 | b1 | W2 | b2 | w3 | b3.
+// Loss: mean over the batch of (y - label)^2.
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_bf16.h>
+
+#include "gx_kernels.h"
+
+namespace gxm {
+
+constexpr int IN = GX_MLP_IN;
+constexpr int H = GX_MLP_HIDDEN;
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + H * IN;
+constexpr int OFF_W2 = OFF_B1 + H;
+constexpr int OFF_B2 = OFF_W2 + H * H;
+constexpr int OFF_W3 = OFF_B2 + H;
+constexpr int OFF_B3 = OFF_W3 + H;
+constexpr int NPARAM = OFF_B3 + 1;
+static_assert(NPARAM == GX_MLP_PARAMS, "parameter count");
+constexpr int LD2 = H + 1;  // padded row of W2 in shared memory (no bank conflicts)
+constexpr int EPB = 16;     // examples per CTA in the training kernel
+
+__device__ __forceinline__ float bf(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
+
+__device__ __forceinline__ float block_sum128(float v, float* red) {
+  // blockDim.x == 128
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  const float t = red[0] + red[1] + red[2] + red[3];
+  __syncthreads();
+  return t;
+}
+
+// Forward (and, with GRAD, backward) of EPB examples per CTA; thread k owns
+// hidden unit k.  Gradients of the mean loss over n examples are added to g.
+template <bool GRAD>
+__global__ void __launch_bounds__(H) mlp_kernel(const float* __restrict__ p, const uint8_t* __restrict__ hist,
+                                                const float* __restrict__ label, uint64_t n,
+                                                const uint64_t* __restrict__ index, float inv_n,
+                                                float* __restrict__ out, float* __restrict__ g,
+                                                float* __restrict__ loss) {
+  extern __shared__ float sm[];
+  float* W2 = sm;                 // [H][LD2]
+  float* gW2 = W2 + H * LD2;      // [H][LD2] (GRAD only)
+  float* h1 = (GRAD ? gW2 + H * LD2 : W2 + H * LD2);  // [H]
+  float* dh2 = h1 + H;            // [H]
+  float* x = dh2 + H;             // [IN]
+  float* red = x + IN;            // [4]
+  const int k = threadIdx.x;
+  for (int i = k; i < H * H; i += H) {
+    W2[(i / H) * LD2 + (i % H)] = bf(p[OFF_W2 + i]);
+    if (GRAD) gW2[(i / H) * LD2 + (i % H)] = 0.f;
+  }
+  float w1[IN];
+#pragma unroll
+  for (int i = 0; i < IN; ++i) w1[i] = bf(p[OFF_W1 + k * IN + i]);
+  const float b1 = p[OFF_B1 + k], b2 = p[OFF_B2 + k], w3 = bf(p[OFF_W3 + k]), b3 = p[OFF_B3];
+  float gw1[IN];
+#pragma unroll
+  for (int i = 0; i < IN; ++i) gw1[i] = 0.f;
+  float gb1 = 0.f, gb2 = 0.f, gw3 = 0.f, gb3 = 0.f, lsum = 0.f;
+  __syncthreads();
+  for (int e = 0; e < EPB; ++e) {
+    const uint64_t slot = (uint64_t)blockIdx.x * EPB + e;
+    if (slot >= n) break;  // uniform in the block
+    const uint64_t ex = index ? index[slot] : slot;
+    if (k < IN) x[k] = hist[ex * IN + k] * (1.0f / 16.0f);
+    __syncthreads();
+    float a1 = b1;
+#pragma unroll
+    for (int i = 0; i < IN; ++i) a1 += w1[i] * x[i];
+    const float z1 = fmaxf(a1, 0.f);
+    h1[k] = z1;
+    __syncthreads();
+    float a2 = b2;
+    for (int j = 0; j < H; ++j) a2 += W2[k * LD2 + j] * h1[j];
+    const float z2 = fmaxf(a2, 0.f);
+    const float y = block_sum128(w3 * z2, red) + b3;
+    if (!GRAD) {
+      if (k == 0) out[ex] = y;
+      continue;
+    }
+    const float dy = 2.f * (y - label[ex]) * inv_n;
+    if (k == 0) lsum += (y - label[ex]) * (y - label[ex]) * inv_n;
+    gb3 += dy;
+    gw3 += dy * z2;
+    const float d2 = a2 > 0.f ? dy * w3 : 0.f;
+    dh2[k] = d2;
+    gb2 += d2;
+    for (int j = 0; j < H; ++j) gW2[k * LD2 + j] += d2 * h1[j];
+    __syncthreads();
+    float s = 0.f;
+    for (int q = 0; q < H; ++q) s += W2[q * LD2 + k] * dh2[q];
+    const float d1 = a1 > 0.f ? s : 0.f;
+    gb1 += d1;
+#pragma unroll
+    for (int i = 0; i < IN; ++i) gw1[i] += d1 * x[i];
+    __syncthreads();
+  }
+  if (!GRAD) return;
+  __syncthreads();
+  for (int i = k; i < H * H; i += H) atomicAdd(&g[OFF_W2 + i], gW2[(i / H) * LD2 + (i % H)]);
+#pragma unroll
+  for (int i = 0; i < IN; ++i) atomicAdd(&g[OFF_W1 + k * IN + i], gw1[i]);
+  atomicAdd(&g[OFF_B1 + k], gb1);
+  atomicAdd(&g[OFF_B2 + k], gb2);
+  atomicAdd(&g[OFF_W3 + k], gw3);
+  if (k == 0) {
+    atomicAdd(&g[OFF_B3], gb3);
+    atomicAdd(loss, lsum);
+  }
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 master parameters; clears the gradient.
+__global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
+                            float* __restrict__ g, float lr, float b1t, float b2t) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= NPARAM) return;
+  const float gi = g[i];
+  const float mi = 0.9f * m[i] + 0.1f * gi;
+  const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / (1.f - b1t)) / (sqrtf(vi / (1.f - b2t)) + 1e-8f);
+  g[i] = 0.f;
+}
+
+// Mini-batch indices: batch element j of step s is example mix64(seed + s * B + j) mod n.
+__global__ void sample_kernel(uint64_t* __restrict__ idx, uint32_t batch, uint64_t n, uint64_t seed,
+                              uint64_t step) {
+  const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= batch) return;
+  uint64_t z = seed + step * batch + j + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  idx[j] = (z ^ (z >> 31)) % n;
+}
+
+size_t smem_bytes(bool grad) { return sizeof(float) * ((grad ? 2 : 1) * H * LD2 + 2 * H + IN + 4); }
+
+}  // namespace gxm
+
+namespace {
+#define GM_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return gx::fail(GX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+gx_status set_smem() {
+  static bool done = false;
+  if (done) return GX_OK;
+  GM_CUDA(cudaFuncSetAttribute(gxm::mlp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)gxm::smem_bytes(true)));
+  GM_CUDA(cudaFuncSetAttribute(gxm::mlp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)gxm::smem_bytes(false)));
+  done = true;
+  return GX_OK;
+}
+}  // namespace
+
+extern "C" {
+
+gx_status gx_mlp_init(float* params, uint64_t seed, void* stream) {
+  gx::clear_error();
+  if (!params) return gx::fail(GX_ERR_INVALID, "params is NULL");
+  // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from a splitmix64 stream, biases 0
+  std::vector<float> h(gxm::NPARAM, 0.f);
+  uint64_t s = seed;
+  auto next = [&]() {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);  // [0, 1)
+  };
+  auto fill = [&](int off, int count, int fan_in) {
+    const double r = 1.0 / std::sqrt((double)fan_in);
+    for (int i = 0; i < count; ++i) h[off + i] = (float)((2.0 * next() - 1.0) * r);
+  };
+  fill(gxm::OFF_W1, gxm::H * gxm::IN, gxm::IN);
+  fill(gxm::OFF_W2, gxm::H * gxm::H, gxm::H);
+  fill(gxm::OFF_W3, gxm::H, gxm::H);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GM_CUDA(cudaMemcpyAsync(params, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
+  GM_CUDA(cudaStreamSynchronize(st));
+  return GX_OK;
+}
+
+gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, float* out, void* stream) {
+  gx::clear_error();
+  if (!params || (n && (!hist || !out))) return gx::fail(GX_ERR_INVALID, "NULL device pointer");
+  if (n == 0) return GX_OK;
+  gx_status s = set_smem();
+  if (s != GX_OK) return s;
+  const uint64_t grid = (n + gxm::EPB - 1) / gxm::EPB;
+  gxm::mlp_kernel<false><<<(unsigned)grid, gxm::H, gxm::smem_bytes(false), static_cast<cudaStream_t>(stream)>>>(
+      params, hist, nullptr, n, nullptr, 0.f, out, nullptr, nullptr);
+  GM_CUDA(cudaGetLastError());
+  return GX_OK;
+}
+
+gx_status gx_mlp_grad(const float* params, const uint8_t* hist, const float* label, uint64_t n,
+                      float* grad, float* loss, void* stream) {
+  gx::clear_error();
+  if (!params || !grad || !loss || (n && (!hist || !label))) return gx::fail(GX_ERR_INVALID, "NULL device pointer");
+  if (n == 0) return GX_OK;
+  gx_status s = set_smem();
+  if (s != GX_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  GM_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * gxm::NPARAM, st));
+  GM_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st));
+  const uint64_t grid = (n + gxm::EPB - 1) / gxm::EPB;
+  gxm::mlp_kernel<true><<<(unsigned)grid, gxm::H, gxm::smem_bytes(true), st>>>(
+      params, hist, label, n, nullptr, 1.0f / (float)n, nullptr, grad, loss);
+  GM_CUDA(cudaGetLastError());
+  return GX_OK;
+}
+
+gx_status gx_mlp_train(float* params, float* state, const uint8_t* hist, const float* label, uint64_t n,
+                       uint32_t batch, uint32_t steps, float lr, uint64_t seed, float* loss, void* stream) {
+  gx::clear_error();
+  if (!params || !state || !hist || !label || !loss) return gx::fail(GX_ERR_INVALID, "NULL device pointer");
+  if (n == 0 || batch == 0) return gx::fail(GX_ERR_INVALID, "empty training set or batch");
+  gx_status s = set_smem();
+  if (s != GX_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float* m = state;
+  float* v = state + gxm::NPARAM;
+  float* g = state + 2 * gxm::NPARAM;
+  uint64_t* idx = reinterpret_cast<uint64_t*>(state + 3 * gxm::NPARAM + 1);  // 8-byte aligned below
+  idx = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(idx) + 7) & ~uintptr_t(7));
+  GM_CUDA(cudaMemsetAsync(state, 0, sizeof(float) * 3 * gxm::NPARAM, st));
+  GM_CUDA(cudaMemsetAsync(loss, 0, sizeof(float) * steps, st));
+  const unsigned grid = (batch + gxm::EPB - 1) / gxm::EPB;
+  double b1t = 1.0, b2t = 1.0;
+  for (uint32_t t = 0; t < steps; ++t) {
+    b1t *= 0.9;
+    b2t *= 0.999;
+    gxm::sample_kernel<<<(batch + 255) / 256, 256, 0, st>>>(idx, batch, n, seed, t);
+    gxm::mlp_kernel<true><<<grid, gxm::H, gxm::smem_bytes(true), st>>>(params, hist, label, batch, idx,
+                                                                       1.0f / (float)batch, nullptr, g,
+                                                                       loss + t);
+    gxm::adam_kernel<<<(gxm::NPARAM + 255) / 256, 256, 0, st>>>(params, m, v, g, lr, (float)b1t, (float)b2t);
+  }
+  GM_CUDA(cudaGetLastError());
+  GM_CUDA(cudaStreamSynchronize(st));
+  return GX_OK;
+}
+
+}  // extern "C"

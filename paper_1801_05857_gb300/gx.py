@@ -51,9 +51,17 @@ class gx_net_desc(ctypes.Structure):
 class gx_explore_opts(ctypes.Structure):
     _fields_ = [("bucket_words", u32), ("group_lanes", u32), ("hash_rounds", u32),
                 ("stop_at_first_deadlock", u32), ("max_levels", u32), ("deadlock_cap", u32),
-                ("ctas_per_sm", u32), ("reserved0", u32), ("table_bytes", u64),
+                ("ctas_per_sm", u32), ("guided_batch", u32), ("table_bytes", u64),
                 ("frontier_states", u64), ("successor_buffer", u64), ("slice_log2", u32),
-                ("partition_min_states", u32)]
+                ("partition_min_states", u32), ("guided_bins", u32), ("guided_scale", ctypes.c_float)]
+
+
+MLP_IN, MLP_HIDDEN = 16, 128
+MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
+
+
+def mlp_state_bytes(batch: int) -> int:
+    return 4 * (3 * MLP_PARAMS + 2) + 8 * batch
 
 
 class gx_stats_t(ctypes.Structure):
@@ -111,6 +119,14 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "gx_probe_random": ([u32, vp, u64, u64, u32, u64, vp, vp], ctypes.c_int),
         "gx_explore_noalloc": ([vp, P(gx_explore_opts), vp, P(gx_stats_t), P(u64), u32, P(u32)],
                                ctypes.c_int),
+        "gx_training_set": ([vp, vp, u64, vp, vp, u32, vp, vp, u64, P(u64)], ctypes.c_int),
+        "gx_mlp_init": ([vp, u64, vp], ctypes.c_int),
+        "gx_mlp_forward": ([vp, vp, u64, vp, vp], ctypes.c_int),
+        "gx_mlp_grad": ([vp, vp, vp, u64, vp, vp, vp], ctypes.c_int),
+        "gx_mlp_train": ([vp, vp, vp, vp, u64, u32, u32, ctypes.c_float, u64, vp, vp], ctypes.c_int),
+        "gx_guided_set_weights": ([vp, vp], ctypes.c_int),
+        "gx_guided_workspace_bytes": ([vp, P(gx_explore_opts), P(u64)], ctypes.c_int),
+        "gx_guided_trace": ([vp, P(u32), u32, P(u32)], ctypes.c_int),
         "gx_batch_create": ([P(vp), u32, P(vp)], ctypes.c_int),
         "gx_batch_free": ([vp], None),
         "gx_batch_workspace_bytes": ([vp, P(gx_batch_opts), P(u64)], ctypes.c_int),
@@ -220,7 +236,7 @@ def default_opts(**kw) -> gx_explore_opts:
     for k, v in kw.items():
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k}")
-        setattr(o, k, int(v))
+        setattr(o, k, float(v) if k == "guided_scale" else int(v))
     return o
 
 
@@ -297,6 +313,79 @@ def explore_noalloc(net: Net, opts: gx_explore_opts | None = None, stream=None,
                                     levels_cap, ctypes.byref(n)))
     stats_d = {name: getattr(s, name) for name, _ in gx_stats_t._fields_ if name != "reserved"}
     return stats_d, [int(x) for x in lv[:min(int(n.value), levels_cap)]]
+
+
+# --------------------------------------------------------------------------------------------
+# learned guidance
+# --------------------------------------------------------------------------------------------
+
+def training_set(net: Net, workspace, max_dist: int, stream=None):
+    """gx_training_set after a gx_explore on net: (hist uint8 (n, 16), label float32 (n,)) tensors."""
+    import torch
+    s = stats(net)
+    dist = torch.empty(s["table_slots"], dtype=torch.int32, device=workspace.device)
+    cap = s["states"]
+    hist = torch.empty((max(cap, 1), 16), dtype=torch.uint8, device=workspace.device)
+    label = torch.empty(max(cap, 1), dtype=torch.float32, device=workspace.device)
+    n = u64()
+    _check(lib().gx_training_set(net.handle, _ptr(workspace), workspace.numel(), _stream(stream), _ptr(dist),
+                                 max_dist, _ptr(hist), _ptr(label), cap, ctypes.byref(n)))
+    k = min(int(n.value), cap)
+    return hist[:k], label[:k]
+
+
+def mlp_init(params, seed: int, stream=None) -> None:
+    _check(lib().gx_mlp_init(_ptr(params), seed, _stream(stream)))
+
+
+def mlp_forward(params, hist, stream=None):
+    import torch
+    out = torch.empty(hist.shape[0], dtype=torch.float32, device=hist.device)
+    _check(lib().gx_mlp_forward(_ptr(params), _ptr(hist), hist.shape[0], _ptr(out), _stream(stream)))
+    return out
+
+
+def mlp_grad(params, hist, label, stream=None):
+    import torch
+    g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=hist.device)
+    loss = torch.empty(1, dtype=torch.float32, device=hist.device)
+    _check(lib().gx_mlp_grad(_ptr(params), _ptr(hist), _ptr(label), hist.shape[0], _ptr(g), _ptr(loss),
+                             _stream(stream)))
+    return g, loss
+
+
+def mlp_train(params, hist, label, batch: int, steps: int, lr: float, seed: int, stream=None):
+    """gx_mlp_train; returns the per-step mini-batch losses (torch tensor)."""
+    import torch
+    state = torch.empty(mlp_state_bytes(batch), dtype=torch.uint8, device=hist.device)
+    loss = torch.empty(steps, dtype=torch.float32, device=hist.device)
+    _check(lib().gx_mlp_train(_ptr(params), _ptr(state), _ptr(hist), _ptr(label), hist.shape[0], batch, steps,
+                              lr, seed, _ptr(loss), _stream(stream)))
+    return loss
+
+
+def guided_set_weights(net: Net, params) -> None:
+    _check(lib().gx_guided_set_weights(net.handle, _ptr(params)))
+    net._guided_params = params  # keep the device buffer alive with the handle
+
+
+def guided_workspace_bytes(net: Net, opts: gx_explore_opts | None = None) -> int:
+    n = u64()
+    _check(lib().gx_guided_workspace_bytes(net.handle, ctypes.byref(opts) if opts else None, ctypes.byref(n)))
+    return int(n.value)
+
+
+def guided_alloc_workspace(net: Net, opts: gx_explore_opts | None = None, device="cuda"):
+    import torch
+    return torch.empty(guided_workspace_bytes(net, opts), dtype=torch.uint8, device=device)
+
+
+def guided_trace(net: Net) -> np.ndarray:
+    n = u32()
+    _check(lib().gx_guided_trace(net.handle, None, 0, ctypes.byref(n)))
+    out = np.zeros((max(int(n.value), 1), net.n_procs), dtype=np.uint32)
+    _check(lib().gx_guided_trace(net.handle, out.ctypes.data_as(P(u32)), int(n.value), ctypes.byref(n)))
+    return out[:int(n.value)].copy()
 
 
 # --------------------------------------------------------------------------------------------

@@ -229,6 +229,70 @@ def random_network(seed: int, n_procs: int, n_states, deg_lo: int = 1, deg_hi: i
     return Network(n_labels, procs, rules, name=name or f"random_s{seed}_n{n_procs}")
 
 
+def planted_network(seed: int, n_procs: int, n_traps: int = 1, n_states: int = 16,
+                    deg_lo: int = 1, deg_hi: int = 3, cluster: int = 3, sync_frac: float = 0.3,
+                    risk_edges: int = 2, name: str = "") -> Network:
+    """Network with planted deadlocks (the guided-search workload).
+
+    Per process: states 0..n_states-3 form a random LTS as in random_network
+    (local edges inside blocks of `cluster` states, some two-party rules), and
+    every one of them keeps at least one local edge, so no process is ever
+    blocked there.  State n_states-2 ("pre-trap") is entered by `risk_edges`
+    local edges from states of the initial block (always including the initial
+    state 0) and leaves by a local edge
+    back to state 0 or by a local "fail" edge into the trap state n_states-1,
+    which has no outgoing edge.  Process 0 has n_traps trap states (the last
+    n_traps indices; the pre-trap is the index before them) with a fail edge
+    into each.  A global state is a deadlock exactly when every process sits in
+    a trap state, so the network has exactly n_traps deadlocks, all reachable.
+    """
+    top = substream(seed, 0)
+    n_labels = 4 * n_procs
+    n_sync = max(1, int(round(sync_frac * n_labels)))
+    # labels: [0, n_sync) rule labels, then per process: a local pool, risk, back, fail
+    rules, member = [], [[] for _ in range(n_procs)]
+    for a in range(n_sync):
+        ps = sorted(top.sample(n_procs, 2))
+        rules.append(Rule([(p, a) for p in ps], a))
+        for p in ps:
+            member[p].append(a)
+    locals_ = list(range(n_sync, n_labels))
+    procs = []
+    for p in range(n_procs):
+        rng = substream(seed, 3, p)
+        traps = n_traps if p == 0 else 1
+        pre = n_states - 1 - traps
+        normal = pre  # states 0..pre-1
+        pool = locals_ + member[p]
+        edges = []
+        for s in range(normal):
+            d = rng.between(deg_lo, deg_hi)
+            seen = set()
+            # one guaranteed local edge, inside the block
+            base = (s // cluster) * cluster
+            t = base + rng.below(min(cluster, normal - base))
+            a = locals_[rng.below(len(locals_))]
+            seen.add((a, t))
+            edges.append((s, a, t))
+            while len(seen) < d:
+                a = pool[rng.below(len(pool))]
+                if a in member[p]:
+                    t = rng.below(normal)
+                else:
+                    t = base + rng.below(min(cluster, normal - base))
+                if (a, t) not in seen:
+                    seen.add((a, t))
+                    edges.append((s, a, t))
+        risk, back, fail = locals_[0], locals_[1], locals_[2]
+        for s in sorted({0} | set(rng.below(min(cluster, normal)) for _ in range(risk_edges - 1))):
+            edges.append((s, risk, pre))
+        edges.append((pre, back, 0))
+        for k in range(traps):
+            edges.append((pre, fail, pre + 1 + k))
+        procs.append(LTS(n_states, 0, edges))
+    return Network(n_labels, procs, rules, name=name or f"planted_s{seed}_n{n_procs}_k{n_traps}")
+
+
 def no_sync_network(seed: int, n_procs: int, n_states: int, deg_lo: int = 0, deg_hi: int = 2,
                     n_labels: int = 4) -> Network:
     """Random network without rules; deg_lo = 0 allows local sink states (deadlocks)."""

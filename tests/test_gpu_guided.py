@@ -1,0 +1,139 @@
+"""Learned guidance for deadlock search, against the oracle.
+
+* Distance labels computed on the GPU equal the oracle's backward BFS.
+* The MLP's forward pass and gradient match a float64 reference.
+* Training lowers the loss.
+* Guided search reports a deadlock with a path the oracle replays step by
+  step, explores fewer states than breadth-first search, and is exhaustive
+  when there is no deadlock.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_1801_05857_gb300 import guide, gx, inputs
+
+pytestmark = pytest.mark.gpu
+
+MAX_DIST = 64
+
+
+def _hist(states):
+    return np.stack([np.bincount(s, minlength=16)[:16] for s in states]).astype(np.int64)
+
+
+@pytest.mark.parametrize("net", [inputs.planted_network(s, n, n_traps=k) for s, n, k in
+                                 ((0, 6, 1), (1, 6, 4), (2, 7, 2), (3, 8, 3))] +
+                         [inputs.random_network(6, 4, 5, 0, 2, 6, n_sync=2, parties=2),
+                          inputs.token_ring(6)], ids=lambda n: n.name)
+def test_labels_equal_oracle_backward_bfs(cuda, net):
+    h = gx.load_network(net)
+    o = gx.default_opts(table_bytes=1 << 24, hash_rounds=32)
+    ws = gx.alloc_workspace(h, o)
+    gx.explore(h, o, ws)
+    hist, label = gx.training_set(h, ws, MAX_DIST)
+    states, dist = oracle.deadlock_distances(net)
+    want = sorted(zip(map(tuple, _hist(states)),
+                      [min(int(d), MAX_DIST) for d in dist]))
+    got = sorted(zip(map(tuple, hist.cpu().numpy().astype(np.int64)),
+                     [int(round(float(x) * MAX_DIST)) for x in label.cpu().numpy()]))
+    assert got == want
+
+
+def test_mlp_forward_and_gradient_match_float64(cuda):
+    import torch
+    p = torch.empty(gx.MLP_PARAMS, dtype=torch.float32, device="cuda")
+    gx.mlp_init(p, 3)
+    rng = np.random.default_rng(1)
+    hist_np = rng.integers(0, 9, size=(1000, 16)).astype(np.uint8)
+    label_np = rng.random(1000).astype(np.float32)
+    hist = torch.from_numpy(hist_np).cuda()
+    label = torch.from_numpy(label_np).cuda()
+    pn = p.cpu().numpy()
+    y = gx.mlp_forward(p, hist).cpu().numpy()
+    yr = omlp.forward(pn, hist_np)
+    assert np.max(np.abs(y - yr) / np.maximum(np.abs(yr), 1e-3)) < 1e-2
+    assert np.max(np.abs(y - yr)) < 1e-4
+    g, loss = gx.mlp_grad(p, hist, label)
+    lr_, gr = omlp.loss_and_grad(pn, hist_np, label_np)
+    g = g.cpu().numpy()
+    assert abs(float(loss.item()) - lr_) <= 1e-4 * lr_ + 1e-7
+    assert np.max(np.abs(g - gr)) <= 1e-3 * np.max(np.abs(gr)) + 1e-7
+
+
+def _trained(steps=600):
+    nets = [inputs.planted_network(s, n, n_traps=1 + s % 4) for s in range(6) for n in (6, 7, 8)]
+    hist, label = guide.collect_examples(nets, MAX_DIST)
+    params, losses = guide.train(hist, label, steps=steps)
+    return params, losses.cpu().numpy()
+
+
+def test_training_lowers_the_loss(cuda):
+    """The histogram features cannot tell which states have lost every path to a
+    deadlock (that depends on the instance's local graphs), so the loss has a floor;
+    training still has to halve it."""
+    _, losses = _trained(400)
+    assert losses[-50:].mean() < 0.5 * losses[:10].mean()
+
+
+def _replay(net, trace):
+    init = [p.initial for p in net.procs]
+    assert list(trace[0]) == init
+    for a, b in zip(trace[:-1], trace[1:]):
+        succ = {tuple(x) for x in oracle.successors(net, a)}
+        assert tuple(b) in succ
+    assert len(oracle.successors(net, trace[-1])) == 0
+
+
+def _guided(net, params, **kw):
+    h = gx.load_network(net)
+    gx.guided_set_weights(h, params)
+    o = gx.default_opts(table_bytes=1 << 27, hash_rounds=32, **kw)
+    ws = gx.guided_alloc_workspace(h, o)
+    n, found = gx.find_deadlocks(h, gx.GX_DL_GUIDED, o, ws)
+    return h, n, found, gx.stats(h)
+
+
+def _bfs_first(net):
+    h = gx.load_network(net)
+    o = gx.default_opts(table_bytes=4 << 30, hash_rounds=32, frontier_states=1 << 27)
+    ws = gx.alloc_workspace(h, o)
+    n, found = gx.find_deadlocks(h, gx.GX_DL_BFS_FIRST, o, ws)
+    return n, gx.stats(h)
+
+
+@pytest.mark.parametrize("seed,n_procs,k", [(10, 9, 1), (11, 10, 3), (12, 12, 2)])
+def test_guided_search_finds_a_replayable_deadlock_faster_than_bfs(cuda, seed, n_procs, k):
+    params, _ = _trained()
+    net = inputs.planted_network(seed, n_procs, n_traps=k)
+    h, n, found, s = _guided(net, params)
+    assert n == 1 and s["deadlock_count"] == 1
+    trace = gx.guided_trace(h)
+    _replay(net, trace)
+    assert list(found[0]) == list(trace[-1])
+    nb, sb = _bfs_first(net)
+    assert nb >= 1
+    assert s["explored"] < sb["explored"]
+
+
+def test_trained_network_beats_untrained(cuda):
+    import torch
+    params, _ = _trained()
+    untrained = torch.empty(gx.MLP_PARAMS, dtype=torch.float32, device="cuda")
+    gx.mlp_init(untrained, 99)
+    net = inputs.planted_network(21, 11, n_traps=2)
+    _, n1, _, s1 = _guided(net, params)
+    _, n2, _, s2 = _guided(net, untrained)
+    assert n1 == 1 and n2 == 1
+    assert s1["explored"] < s2["explored"]
+
+
+def test_guided_search_without_deadlock_is_exhaustive(cuda):
+    params, _ = _trained(100)
+    net = inputs.token_ring(8)
+    h, n, found, s = _guided(net, params, guided_batch=256)
+    assert n == 0 and s["complete"] == 1 and s["deadlock_count"] == 0
+    r = oracle.explore(net)
+    assert s["states"] == r.states and s["explored"] == r.states
+    assert s["transitions"] == r.transitions

@@ -233,3 +233,48 @@ def test_device_key_sequence_has_the_same_keys():
         a = inputs.key_sequence_device(2100, d, seed=5, device="cpu").numpy().view(np.uint32)
         b = inputs.key_sequence(2100, d, words=1, seed=5)[:, 0]
         assert sorted(a.tolist()) == sorted(b.tolist())
+
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    """Pins oracle/mlp.py's backward pass: central differences in float64 on the
+    unrounded network agree with the analytic gradient."""
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    p = (rng.standard_normal(mlp.NPARAM) * 0.2).astype(np.float32)
+    hist = rng.integers(0, 5, size=(12, 16))
+    label = rng.random(12)
+    _, g = mlp.loss_and_grad(p, hist, label, bf16=False)
+    pd = p.astype(np.float64)
+
+    def loss_at(q):
+        W1, b1, W2, b2, w3, b3 = mlp.unpack(q.astype(np.float32))  # layout only
+        x = hist / 16.0
+        a1 = x @ q[:mlp.H * mlp.IN].reshape(mlp.H, mlp.IN).T + q[mlp.H * mlp.IN:mlp.H * mlp.IN + mlp.H]
+        o = mlp.H * mlp.IN + mlp.H
+        W2q = q[o:o + mlp.H * mlp.H].reshape(mlp.H, mlp.H); o += mlp.H * mlp.H
+        b2q = q[o:o + mlp.H]; o += mlp.H
+        w3q = q[o:o + mlp.H]; o += mlp.H
+        y = np.maximum(np.maximum(a1, 0) @ W2q.T + b2q, 0) @ w3q + q[o]
+        return np.mean((y - label) ** 2)
+
+    idx = np.concatenate([rng.choice(mlp.H * mlp.IN, 20, replace=False),
+                          mlp.H * mlp.IN + mlp.H + rng.choice(mlp.H * mlp.H, 30, replace=False),
+                          [mlp.NPARAM - 1], mlp.NPARAM - 1 - mlp.H + rng.choice(mlp.H, 10, replace=False)])
+    for i in idx:
+        e = np.zeros_like(pd)
+        e[i] = 1e-6
+        fd = (loss_at(pd + e) - loss_at(pd - e)) / 2e-6
+        assert abs(fd - g[i]) <= 1e-5 + 1e-4 * abs(g[i]), (i, fd, g[i])
+
+
+def test_bf16_rounding_definition():
+    """bfloat16 keeps the upper 16 bits of binary32, rounding to nearest, ties to even."""
+    from oracle import mlp
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1.0 + 2 ** -9, -2.5, 3.140625], dtype=np.float32)
+    r = mlp.bf16_round(x)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                      # halfway: tie to even (mantissa ...0)
+    assert r[2] == np.float32(1.0 + 4 * 2 ** -8)  # halfway: tie to even (rounds up)
+    assert r[3] == 1.0
+    assert r[4] == -2.5 and r[5] == np.float32(3.140625)
+    assert ((r.view(np.uint32) & 0xFFFF) == 0).all()
