@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-table", action="store_true", help="skip the Sec. 5.1 find-or-put part")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
+    ap.add_argument("--no-guided", action="store_true", help="skip the guided deadlock-search part")
     ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
                          "exploration for every (bucket, group) size; one JSON line per point")
@@ -268,6 +269,67 @@ def batched_part(torch, gx, inputs, steps: int = 5) -> dict:
             "speedup_vs_sequential": round(seq * 1e3 / med, 2)}
 
 
+def guided_part(torch, gx, inputs, guide) -> dict:
+    """Learned guided deadlock search vs breadth-first search on 12-16-process networks
+    with planted deadlocks; the scoring network is trained on 6-8-process instances."""
+    t0 = time.perf_counter()
+    train_nets = [inputs.planted_network(s, n, n_traps=1 + s % 4) for s in range(6) for n in (6, 7, 8)]
+    hist, label = guide.collect_examples(train_nets, 64)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    params, losses = guide.train(hist, label, steps=1500)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    untrained = torch.empty(gx.MLP_PARAMS, dtype=torch.float32, device="cuda")
+    gx.mlp_init(untrained, 99)
+
+    def guided(net, p):
+        h = gx.load_network(net)
+        gx.guided_set_weights(h, p)
+        o = gx.default_opts(table_bytes=2 << 30, hash_rounds=32)
+        ws = gx.guided_alloc_workspace(h, o)
+        try:
+            n, _ = gx.find_deadlocks(h, gx.GX_DL_GUIDED, o, ws)
+            s = gx.stats(h)
+            return {"found": n, "explored": s["explored"], "stored": s["states"], "ms": round(s["gpu_ms"], 3),
+                    "path_states": len(gx.guided_trace(h)), "iterations": s["expand_launches"]}
+        except gx.GxError as e:
+            return {"error": STATUS(e)}
+        finally:
+            del ws
+            torch.cuda.empty_cache()
+
+    def bfs(net):
+        h = gx.load_network(net)
+        o = gx.default_opts(table_bytes=24 << 30, hash_rounds=32, frontier_states=1 << 30)
+        ws = gx.alloc_workspace(h, o)
+        try:
+            n, _ = gx.find_deadlocks(h, gx.GX_DL_BFS_FIRST, o, ws)
+            s = gx.stats(h)
+            return {"found": n, "explored": s["explored"], "stored": s["states"], "ms": round(s["gpu_ms"], 3),
+                    "first_deadlock_level": s["first_deadlock_level"]}
+        except gx.GxError as e:
+            return {"error": STATUS(e)}
+        finally:
+            del ws
+            torch.cuda.empty_cache()
+
+    rows = []
+    for seed, n, k in ((1, 12, 2), (0, 13, 2), (1, 14, 2), (2, 16, 3)):
+        net = inputs.planted_network(seed, n, n_traps=k)
+        rows.append({"network": net.name, "processes": n, "planted_deadlocks": k,
+                     "guided": guided(net, params), "untrained": guided(net, untrained), "bfs": bfs(net)})
+    lo = losses.cpu().numpy()
+    return {"train": {"networks": len(train_nets), "examples": int(hist.shape[0]),
+                      "label_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3), "steps": 1500,
+                      "loss_first": round(float(lo[:10].mean()), 4), "loss_last": round(float(lo[-50:].mean()), 4)},
+            "instances": rows}
+
+
+def STATUS(e) -> str:
+    return str(e).split(":")[0]
+
+
 def cpu_baseline(net, sample: int) -> dict:
     import oracle
     r = oracle.explore(net, max_explored=sample)
@@ -388,6 +450,10 @@ def run_ours(args, world, rank, local, pg):
     batch_part = None
     if rank == 0 and not args.no_batch:
         batch_part = batched_part(torch, gx, inputs)
+    guided_res = None
+    if rank == 0 and not args.no_guided:
+        from paper_1801_05857_gb300 import guide
+        guided_res = guided_part(torch, gx, inputs, guide)
 
     # end to end through the public API with host-resident inputs: load the network
     # description from host arrays, explore with a library-allocated workspace, read the
@@ -433,6 +499,7 @@ def run_ours(args, world, rank, local, pg):
             "roofline": roof,
             "find_or_put": table_part,
             "batched": batch_part,
+            "guided_deadlock_search": guided_res,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps * (1 + launches // args.steps),

@@ -269,7 +269,8 @@ gx_status gx_mlp_train(float* params, float* state, const uint8_t* hist, const f
 gx_status gx_guided_set_weights(gx_net* net, const float* params);
 
 /* Workspace bytes for a GX_DL_GUIDED search (table, priority bins, the log of
- * expanded states with their parents). */
+ * expanded states with their parents).  The bins together hold one entry per
+ * table slot (a full bin spills into the next one), the log one per slot. */
 gx_status gx_guided_workspace_bytes(const gx_net* net, const gx_explore_opts* opts, uint64_t* bytes);
 
 /* The path of the deadlock found by the last GX_DL_GUIDED search: up to cap

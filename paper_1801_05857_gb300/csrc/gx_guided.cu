@@ -281,9 +281,12 @@ template <int W>
 __device__ __forceinline__ void push_bin(const GuidedArgs& a, float score, const uint32_t (&v)[W], uint32_t parent,
                                          uint32_t& err) {
   constexpr int E = W + 1;
-  int b = (int)(score / a.scale * (float)a.nbins);
-  b = b < 0 ? 0 : (b >= a.nbins ? a.nbins - 1 : b);
-  for (; b < a.nbins; ++b) {  // a full bin spills into the next (worse) one
+  int b0 = (int)(score / a.scale * (float)a.nbins);
+  b0 = b0 < 0 ? 0 : (b0 >= a.nbins ? a.nbins - 1 : b0);
+  // a full bin spills into the next one (cyclically): the bins together hold
+  // as many entries as the table has slots, so some bin always has room
+  for (int i = 0; i < a.nbins; ++i) {
+    const int b = (b0 + i) % a.nbins;
     const unsigned long long pos = atomicAdd(&a.bin_count[b], 1ull);
     if (pos < a.bin_cap) {
       uint32_t* e = a.bins + ((uint64_t)b * a.bin_cap + pos) * E;
@@ -535,7 +538,7 @@ gx_status guided_plan(const Net& net, const gx_explore_opts* o, GPlan& P) {
   P.nb = nb;
   P.slots = nb * (uint64_t)(P.B / P.W);
   P.log_cap = P.slots;                                   // every state is expanded at most once
-  P.bin_cap = std::max<uint64_t>(P.batch_cap, P.slots / 4);
+  P.bin_cap = std::max<uint64_t>(P.batch_cap, (P.slots + P.nbins - 1) / P.nbins + 1);
   const uint64_t E = (uint64_t)P.W + 1;
   uint64_t off = 0;
   P.off_ctl = off;
