@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--rounds", type=int, default=32)
     ap.add_argument("--table-log2-words", type=int, default=28)
     ap.add_argument("--slice-log2", type=int, default=0)
+    ap.add_argument("--nodes", type=int, default=19, help="token-ring nodes for --experiment scaled")
     ap.add_argument("--partition-min", type=int, default=0,
                     help="partition levels with at least this many states (0 = never)")
     ap.add_argument("--cpu-sample", type=int, default=3_000_000,
@@ -52,7 +53,7 @@ def parse():
     ap.add_argument("--no-table", action="store_true", help="skip the Sec. 5.1 find-or-put part")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided deadlock-search part")
-    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep"],
+    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep", "scaled"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
                          "exploration for every (bucket, group) size; one JSON line per point")
     return ap.parse_args()
@@ -508,6 +509,58 @@ def run_ours(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def scaled_experiment(torch, gx, inputs, args):
+    """Memory-scaled exploration: the token ring with --nodes nodes (2N 3^(N-1) states,
+    4 N^2 3^(N-2) transitions) in a table of 2^--table-log2-words words; one line per
+    level with the table fill after it, then a summary binned by fill."""
+    n = args.nodes
+    net = inputs.token_ring(n)
+    h = gx.load_network(net)
+    o = gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
+                        table_bytes=4 << args.table_log2_words, slice_log2=args.slice_log2,
+                        partition_min_states=args.partition_min)
+    ws = gx.alloc_workspace(h, o)
+    gx.explore(h, o, ws)
+    s = gx.stats(h)
+    lv = gx.levels(h)
+    prof = gx.level_profile(h)
+    want_states = 2 * n * 3 ** (n - 1)
+    want_trans = 4 * n * n * 3 ** (n - 2)
+    W = s["slot_words"]
+    bucket_bytes = max(32, 4 * s["bucket_words"])
+    found = 1
+    bins = {}
+    for k, ms in enumerate(prof["ms"]):
+        new = lv[k + 1] if k + 1 < len(lv) else 0
+        explored = lv[k]
+        found += new
+        fill = found / s["table_slots"]
+        byts = prof["probes"][k] * bucket_bytes + new * (32 + 4 * W) + explored * 4 * W
+        rec = {"experiment": "scaled", "level": k, "expanded": explored, "new": new, "fill_after": round(fill, 4),
+               "ms": round(ms, 3), "new_states_per_s": round(new / (ms * 1e-3), 1) if ms else None,
+               "algorithmic_gbs": round(byts / (ms * 1e-3) / 1e9, 1) if ms else None,
+               "probes_per_successor": round(prof["probes"][k] / max(prof["transitions"][k], 1), 4)}
+        print(json.dumps(rec), flush=True)
+        b = min(int(fill * 10), 9)
+        acc = bins.setdefault(b, [0, 0.0, 0])
+        acc[0] += new
+        acc[1] += ms
+        acc[2] += byts
+    summary = {"experiment": "scaled-summary", "network": net.name, "states": s["states"],
+               "states_closed_form": want_states, "transitions": s["transitions"],
+               "transitions_closed_form": want_trans, "levels": len(lv), "table_slots": s["table_slots"],
+               "table_gib": round(4 * s["table_slots"] * W / 2 ** 30, 1), "fill": round(s["fill"], 4),
+               "bucket_words": s["bucket_words"], "group_lanes": s["group_lanes"], "gpu_ms": round(s["gpu_ms"], 1),
+               "partitioned_levels": s["partitioned_levels"], "slice_log2": args.slice_log2,
+               "states_per_s": round(s["states"] / (s["gpu_ms"] * 1e-3), 1),
+               "by_fill_decile": {f"{10 * b}-{10 * b + 10}%": {"new_states": v[0], "ms": round(v[1], 1),
+                                                              "states_per_s": round(v[0] / (v[1] * 1e-3), 1) if v[1] else None,
+                                                              "algorithmic_gbs": round(v[2] / (v[1] * 1e-3) / 1e9, 1) if v[1] else None}
+                                  for b, v in sorted(bins.items())}}
+    print(json.dumps(summary), flush=True)
+    assert s["states"] == want_states and s["transitions"] == want_trans, "closed form mismatch"
+
+
 def run_experiment(args):
     """One JSON line per point; not the bench contract's line."""
     import torch
@@ -526,6 +579,8 @@ def run_experiment(args):
                     print(json.dumps({"experiment": "sec5.1 find-or-put", **pt}), flush=True)
                     group *= 2
             del keys
+    elif args.experiment == "scaled":
+        scaled_experiment(torch, gx, inputs, args)
     elif args.experiment == "bucket-sweep":
         net = inputs.workload(args.workload)
         h = gx.load_network(net)

@@ -202,6 +202,13 @@ gx_status gx_stats(const gx_net* net, gx_stats_t* out);
  * Writes min(cap, n_levels) entries; *n_levels gets the total. */
 gx_status gx_levels(const gx_net* net, uint64_t* out, uint32_t cap, uint32_t* n_levels);
 
+/* Per expanded level of the last gx_explore / BFS search (level k expands the
+ * states of level k into level k + 1): device time in ms (CUDA events around
+ * the level's kernels), buckets read by find-or-put, and successors generated.
+ * Any output may be NULL; writes min(cap, n) entries, *n gets the count. */
+gx_status gx_level_profile(const gx_net* net, double* ms, uint64_t* probes, uint64_t* transitions,
+                           uint32_t cap, uint32_t* n);
+
 /* Deadlock states kept by the last search (at most opts.deadlock_cap), n_procs
  * local states each, in no particular order.  *n gets the number written. */
 gx_status gx_deadlocks(const gx_net* net, uint32_t* out, uint32_t cap, uint32_t* n);

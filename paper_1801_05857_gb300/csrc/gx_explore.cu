@@ -162,9 +162,9 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
   if ((1ull << P.logp) > P.nb) P.logp = ilog2(P.nb);
   P.part_min = o->partition_min_states;
   if (P.part_min == 0) P.logp = 0;  // path off
-  P.cs = o->successor_buffer ? o->successor_buffer : slots / 2;
+  P.cs = o->successor_buffer ? o->successor_buffer : std::min<uint64_t>(slots / 2, (1ull << 32) - 1);
+  if (P.logp == 0) P.cs = 0;  // partitioned path off: no buffer
   if (P.cs >= (1ull << 32)) return fail(GX_ERR_INVALID, "successor_buffer must be below 2^32 vectors");
-  if (P.logp == 0) P.cs = 0;
   uint64_t off = 0;
   P.off_ctl = off;
   off = align_up(off + sizeof(Ctl));
@@ -328,6 +328,9 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   double expand_ms = 0;
   uint64_t launches = 0, levels_done = 0;
   uint32_t err = 0;
+  std::vector<double> lv_ms;
+  std::vector<uint64_t> lv_probes, lv_trans;
+  uint64_t prev_probes = 0, prev_trans = 0;
   bool complete = false;
   // partitioned path set-up
   PartArgs pa{};
@@ -400,6 +403,11 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
     GX_CUDA(cudaEventElapsedTime(&ms, ek0, ek1));
     expand_ms += ms;
     ++levels_done;
+    lv_ms.push_back(ms);
+    lv_probes.push_back(hc->probes - prev_probes);
+    lv_trans.push_back(hc->transitions - prev_trans);
+    prev_probes = hc->probes;
+    prev_trans = hc->transitions;
     explored += cur_end - cur_begin;
     if (first_dl < 0 && hc->dl_count > 0) first_dl = (int64_t)levels.size() - 1;
     err = hc->error;
@@ -460,6 +468,9 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   S.h2d_bytes = 4ull * net.blob.size();
   S.d2h_bytes = sizeof(Ctl) * levels_done + 4ull * dlw.size() + d2h_tot;
   h->levels = levels;
+  h->level_ms = lv_ms;
+  h->level_probes = lv_probes;
+  h->level_transitions = lv_trans;
   h->ws_off_ctl = P.off_ctl;
   h->ws_off_blob = P.off_blob;
   h->ws_off_table = P.off_table;
@@ -533,6 +544,21 @@ gx_status gx_levels(const gx_net* h, uint64_t* out, uint32_t cap, uint32_t* n_le
   if (cap && !out) return gx::fail(GX_ERR_INVALID, "out is NULL");
   for (size_t i = 0; i < h->levels.size() && i < cap; ++i) out[i] = h->levels[i];
   if (n_levels) *n_levels = (uint32_t)h->levels.size();
+  return GX_OK;
+}
+
+gx_status gx_level_profile(const gx_net* h, double* ms, uint64_t* probes, uint64_t* transitions, uint32_t cap,
+                           uint32_t* n) {
+  gx::clear_error();
+  if (!h) return gx::fail(GX_ERR_INVALID, "net is NULL");
+  if (!h->have_result) return gx::fail(GX_ERR_STATE, "no search has run on this network");
+  const size_t k = h->level_ms.size();
+  for (size_t i = 0; i < k && i < cap; ++i) {
+    if (ms) ms[i] = h->level_ms[i];
+    if (probes) probes[i] = h->level_probes[i];
+    if (transitions) transitions[i] = h->level_transitions[i];
+  }
+  if (n) *n = (uint32_t)k;
   return GX_OK;
 }
 

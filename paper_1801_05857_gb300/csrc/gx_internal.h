@@ -55,6 +55,9 @@ struct gx_net {
   bool have_result = false;
   gx_stats_t stats{};
   std::vector<uint64_t> levels;
+  // per expanded level: device time, buckets read, transitions
+  std::vector<double> level_ms;
+  std::vector<uint64_t> level_probes, level_transitions;
   std::vector<uint32_t> deadlocks;  // unpacked, n_procs per state
   // workspace regions of the last search (for gx_set_digest, gx_training_set)
   uint64_t ws_off_ctl = 0, ws_off_blob = 0, ws_off_table = 0, ws_total = 0;

@@ -114,6 +114,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "gx_stats": ([vp, P(gx_stats_t)], ctypes.c_int),
         "gx_levels": ([vp, P(u64), u32, P(u32)], ctypes.c_int),
         "gx_deadlocks": ([vp, P(u32), u32, P(u32)], ctypes.c_int),
+        "gx_level_profile": ([vp, P(ctypes.c_double), P(u64), P(u64), u32, P(u32)], ctypes.c_int),
         "gx_set_digest": ([vp, vp, u64, vp, P(u64), P(u64), P(u64)], ctypes.c_int),
         "gx_find_or_put": ([vp, u64, u32, u32, u32, u32, vp, u64, vp, vp, vp], ctypes.c_int),
         "gx_probe_random": ([u32, vp, u64, u64, u32, u64, vp, vp], ctypes.c_int),
@@ -285,6 +286,19 @@ def levels(net: Net) -> list:
     out = np.zeros(max(int(n.value), 1), dtype=np.uint64)
     _check(lib().gx_levels(net.handle, out.ctypes.data_as(P(u64)), int(n.value), ctypes.byref(n)))
     return [int(x) for x in out[:int(n.value)]]
+
+
+def level_profile(net: Net) -> dict:
+    """gx_level_profile: per expanded level, device ms, buckets read and successors."""
+    n = u32()
+    _check(lib().gx_level_profile(net.handle, None, None, None, 0, ctypes.byref(n)))
+    k = int(n.value)
+    ms = np.zeros(max(k, 1), dtype=np.float64)
+    pr = np.zeros(max(k, 1), dtype=np.uint64)
+    tr = np.zeros(max(k, 1), dtype=np.uint64)
+    _check(lib().gx_level_profile(net.handle, ms.ctypes.data_as(P(ctypes.c_double)), pr.ctypes.data_as(P(u64)),
+                                  tr.ctypes.data_as(P(u64)), k, ctypes.byref(n)))
+    return dict(ms=ms[:k].tolist(), probes=[int(x) for x in pr[:k]], transitions=[int(x) for x in tr[:k]])
 
 
 def deadlocks(net: Net, cap: int = 1 << 20) -> np.ndarray:
