@@ -149,6 +149,22 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": mx, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def ncu_traffic(args) -> dict | None:
+    """DRAM bytes of the expansion kernel from the committed ncu capture, when it was taken
+    on this workload and configuration and the kernel sources have not changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "expand_kernel_mid_traffic.json")
+    if not os.path.exists(path) or args.workload != "mid" or (args.bucket, args.group) != (8, 1) \
+            or args.table_log2_words != 28:
+        return None
+    with open(path) as f:
+        t = json.load(f)
+    src = b"".join(open(os.path.join(ROOT, p), "rb").read() for p in t["kernel_sources"])
+    if hashlib.sha256(src).hexdigest() != t["kernel_sources_sha256"]:
+        return None
+    return t
+
+
 def algorithmic_bytes(s: dict) -> int:
     """Bytes the level-expansion kernels must move, per search:
     every bucket read is at least one 32-byte sector (a B-word bucket is
@@ -420,8 +436,13 @@ def run_ours(args, world, rank, local, pg):
     bytes_per_search = algorithmic_bytes(s_avg)
     exp_ms_per_search = expand_ms / args.steps
     achieved = bytes_per_search / (exp_ms_per_search * 1e-3) / 1e9
+    tr = ncu_traffic(args)
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": None,
+            "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "traffic": tr["dram_bytes_per_launch"] if tr else None,
+            "traffic_source": "profiles/expand_kernel_mid_traffic.json (ncu dram__bytes_read.sum + "
+                              "dram__bytes_write.sum, bytes per launch)" if tr else "no capture for this kernel",
+            "algorithmic_bytes_per_launch": bytes_per_search // max(launches // args.steps, 1),
             "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, sequential copy)",
             "kernel": "expand_kernel", "launches_per_step": launches // args.steps,
             "avg_launch_ms": round(expand_ms / max(launches, 1), 4),
