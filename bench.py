@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--table-log2-words", type=int, default=28)
     ap.add_argument("--slice-log2", type=int, default=0)
     ap.add_argument("--nodes", type=int, default=19, help="token-ring nodes for --experiment scaled")
+    ap.add_argument("--warp-cache", type=int, default=9,
+                    help="log2 entries of the per-warp cache of seen vectors (0 = off)")
     ap.add_argument("--partition-min", type=int, default=0,
                     help="partition levels with at least this many states (0 = never)")
     ap.add_argument("--cpu-sample", type=int, default=3_000_000,
@@ -155,7 +157,7 @@ def ncu_traffic(args) -> dict | None:
     import hashlib
     path = os.path.join(ROOT, "profiles", "expand_kernel_mid_traffic.json")
     if not os.path.exists(path) or args.workload != "mid" or (args.bucket, args.group) != (8, 1) \
-            or args.table_log2_words != 28:
+            or args.table_log2_words != 28 or args.warp_cache != 9:
         return None
     with open(path) as f:
         t = json.load(f)
@@ -395,7 +397,7 @@ def run_ours(args, world, rank, local, pg):
     table_bytes = 4 << args.table_log2_words
     opts = gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
                            table_bytes=table_bytes, slice_log2=args.slice_log2,
-                           partition_min_states=args.partition_min)
+                           partition_min_states=args.partition_min, warp_cache_log2=args.warp_cache)
     ws = gx.alloc_workspace(h, opts)
     st = torch.cuda.current_stream()
 
@@ -539,7 +541,7 @@ def scaled_experiment(torch, gx, inputs, args):
     h = gx.load_network(net)
     o = gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
                         table_bytes=4 << args.table_log2_words, slice_log2=args.slice_log2,
-                        partition_min_states=args.partition_min)
+                        partition_min_states=args.partition_min, warp_cache_log2=args.warp_cache)
     ws = gx.alloc_workspace(h, o)
     gx.explore(h, o, ws)
     s = gx.stats(h)
@@ -610,7 +612,8 @@ def run_experiment(args):
             group = 1
             while bucket >= W and group <= bucket // W:
                 o = gx.default_opts(bucket_words=bucket, group_lanes=group, hash_rounds=args.rounds,
-                                    table_bytes=4 << args.table_log2_words)
+                                    table_bytes=4 << args.table_log2_words,
+                                    warp_cache_log2=args.warp_cache)
                 ws = gx.alloc_workspace(h, o)
                 ts = []
                 for _ in range(args.warmup + args.steps):

@@ -242,6 +242,35 @@ struct WarpStage {
   }
 };
 
+// Per-warp cache of recently seen vectors (the block-local state cache of
+// Fig. 2, in shared memory, per warp): direct-mapped, overwritten on a miss,
+// never cleared.  Every vector written into it is passed to find-or-put by the
+// lane that wrote it, so a hit means the vector is in the table or being put
+// there by this warp, and its find-or-put can be skipped.  Only for 1- and
+// 2-word vectors, whose entries are read and written by single aligned
+// shared-memory accesses (a torn entry could otherwise fake a hit).
+struct WarpCache {
+  uint32_t* base;  // 2^log2 entries of W words, or nullptr
+  uint32_t mask;
+  template <int W>
+  __device__ __forceinline__ bool seen(uint64_t h, const uint32_t (&v)[W]) const {
+    if constexpr (W == 1) {
+      uint32_t* e = base + ((uint32_t)h & mask);
+      if (*e == v[0]) return true;
+      *e = v[0];
+      return false;
+    } else if constexpr (W == 2) {
+      unsigned long long* e = reinterpret_cast<unsigned long long*>(base) + ((uint32_t)h & mask);
+      const unsigned long long x = (unsigned long long)v[0] | ((unsigned long long)v[1] << 32);
+      if (*e == x) return true;
+      *e = x;
+      return false;
+    } else {
+      return false;
+    }
+  }
+};
+
 // Successors each lane generates per round.  insert_lanes takes K per lane
 // (the group issues the first-bucket loads of up to four items before it
 // resolves any of them); measured on the mid network, K = 2 or 4 costs more in
@@ -261,7 +290,8 @@ template <int W, int B, int G, int K>
 __device__ __forceinline__ void insert_lanes(const Target& a, const uint64_t* muls,
                                              const Group<G>& g, const bool (&has)[K],
                                              const uint32_t (&s)[K][W], uint32_t& probes,
-                                             uint32_t& err, WarpStage& st) {
+                                             uint32_t& err, WarpStage& st,
+                                             const WarpCache& cache = WarpCache{nullptr, 0}) {
   constexpr int LW = (B / W / G) * W;
   constexpr int NI = G * K;            // items of the group this round
   constexpr int CH = NI < 4 ? NI : 4;  // items in flight at a time
@@ -280,6 +310,11 @@ __device__ __forceinline__ void insert_lanes(const Target& a, const uint64_t* mu
       hv[j] = g.template bcast<int>(has[i % K] ? 1 : 0, src) != 0;  // uniform in the group
 #pragma unroll
       for (int w = 0; w < W; ++w) x[j][w] = g.template bcast<uint32_t>(s[i % K][w], src);
+      if (hv[j]) {
+        const uint64_t hh = vec_hash<W>(x[j]);
+        // a vector this warp has already sent to find-or-put needs no second lookup
+        if (cache.base && cache.template seen<W>(hh, x[j])) hv[j] = false;
+      }
       if (hv[j]) {
         const uint64_t b = bucket_of(vec_hash<W>(x[j]), muls[0], a.log2nb);
         load_words<LW>(a.table + b * (uint64_t)B + (uint64_t)g.glane * LW, pre[j]);
@@ -319,6 +354,15 @@ __global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
   const Target tg = target_of(a);
+  WarpCache cache{nullptr, 0};
+  if (W <= 2 && a.cache_log2 > 0) {
+    uint32_t* cbase = sm + 2 * kMaxRounds + (a.stage ? a.blob_words : 0);
+    const uint32_t per_warp = (1u << a.cache_log2) * W;
+    cache.base = cbase + (threadIdx.x >> 5) * per_warp;
+    cache.mask = (1u << a.cache_log2) - 1u;
+    for (uint32_t i = lane; i < per_warp; i += 32) cache.base[i] = 0u;  // 0 is never a stored vector
+    __syncwarp();
+  }
 
   while (true) {
     unsigned long long chunk = 0;
@@ -358,7 +402,7 @@ __global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(
           for (int w = 0; w < W; ++w) s[k][w] = 0;
         }
       }
-      insert_lanes<W, B, G, K>(tg, muls, g, has, s, probes, err, st);
+      insert_lanes<W, B, G, K>(tg, muls, g, has, s, probes, err, st, cache);
     }
   }
   st.flush<W>(tg, err);

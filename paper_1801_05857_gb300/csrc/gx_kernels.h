@@ -47,6 +47,7 @@ struct ExpandArgs {
   Ctl* ctl;
   uint32_t* dl_buf;          // deadlock vectors, W words each
   uint32_t dl_cap;
+  int cache_log2;            // per-warp cache of recently seen vectors: 2^cache_log2 entries (0 = off)
 };
 
 // Partitioned expansion of one level (or one batch of it): successors are

@@ -231,6 +231,7 @@ gx_status gx_default_opts(gx_explore_opts* o) {
   o->bucket_words = 8;
   o->hash_rounds = 8;
   o->deadlock_cap = 1024;
+  o->warp_cache_log2 = 9;
   return GX_OK;
 }
 

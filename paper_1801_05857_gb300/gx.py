@@ -53,7 +53,8 @@ class gx_explore_opts(ctypes.Structure):
                 ("stop_at_first_deadlock", u32), ("max_levels", u32), ("deadlock_cap", u32),
                 ("ctas_per_sm", u32), ("guided_batch", u32), ("table_bytes", u64),
                 ("frontier_states", u64), ("successor_buffer", u64), ("slice_log2", u32),
-                ("partition_min_states", u32), ("guided_bins", u32), ("guided_scale", ctypes.c_float)]
+                ("partition_min_states", u32), ("guided_bins", u32), ("warp_cache_log2", u32),
+                ("guided_scale", ctypes.c_float)]
 
 
 MLP_IN, MLP_HIDDEN = 16, 128

@@ -80,4 +80,4 @@ def test_stats_before_search_is_a_state_error():
 
 def test_default_opts_values():
     o = gx.default_opts()
-    assert (o.bucket_words, o.hash_rounds, o.deadlock_cap) == (8, 8, 1024)
+    assert (o.bucket_words, o.hash_rounds, o.deadlock_cap, o.warp_cache_log2) == (8, 8, 1024, 9)

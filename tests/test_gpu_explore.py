@@ -225,3 +225,34 @@ def test_partitioned_buffer_too_small_falls_back(cuda):
     s = assert_parity(inputs.token_ring(10), table_bytes=1 << 22, slice_log2=2, successor_buffer=1,
                       partition_min_states=1)
     assert s["partitioned_levels"] < s["n_levels"] - 1  # only levels with one successor fit
+
+
+@pytest.mark.parametrize("cache_log2", [4, 9, 11])
+@pytest.mark.parametrize("net", [inputs.token_ring(10), inputs.token_ring(12),
+                                 inputs.random_network(7, 6, 8, 1, 3, 8, n_sync=2, parties=2),
+                                 inputs.random_network(1, 10, 16, 1, 3, 12, n_sync=4, parties=2, cluster=4),
+                                 inputs.random_network(6, 8, 8, 0, 2, 10, n_sync=4, parties=2)],
+                         ids=lambda n: n.name)
+def test_warp_cache_keeps_results_exact(cuda, net, cache_log2):
+    """The per-warp cache of seen vectors only skips lookups; every count stays exact
+    (a 16-entry cache is overwritten all the time, a 4096-entry one rarely)."""
+    for B, G in ((8, 1), (16, 2)):
+        assert_parity(net, table_bytes=1 << 27, bucket_words=B, group_lanes=G, hash_rounds=32,
+                      warp_cache_log2=cache_log2)
+
+
+def test_warp_cache_too_large_is_rejected(cuda):
+    h = gx.load_network(inputs.token_ring(12))
+    o = gx.default_opts(table_bytes=1 << 27, warp_cache_log2=12)
+    with pytest.raises(gx.GxError) as e:
+        gx.explore(h, o, gx.alloc_workspace(h, o))
+    assert e.value.status == gx.GX_ERR_INVALID and "shared memory" in e.value.message
+
+
+def test_mid_config_with_warp_cache(cuda):
+    g = _golden_case("mid_network.json")
+    net = inputs.random_network(**g["generator"])
+    h, s, lv, ws = run_gpu(net, table_bytes=4 << 28, bucket_words=8, group_lanes=1, hash_rounds=32,
+                           warp_cache_log2=9)
+    assert (s["states"], s["transitions"], lv) == (g["states"], g["transitions"], g["levels"])
+    assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])
