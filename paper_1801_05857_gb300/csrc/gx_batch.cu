@@ -168,15 +168,25 @@ __global__ void __launch_bounds__(1024) batch_advance_kernel(const BatchArgs a, 
   }
 }
 
+// Per-warp cache of seen vectors in the batched kernel (1- and 2-word slots).
+// Networks have separate tables, so a hit is only valid for the network whose
+// vectors filled the cache: a warp clears its cache whenever it moves to a
+// chunk of another network.
+constexpr int kBatchCacheLog2 = 9;
+
 template <int W, int B, int G>
 __global__ void __launch_bounds__(gx::kBlock) batch_expand_kernel(const BatchArgs a) {
   __shared__ uint64_t muls[kMaxRounds];
   for (int i = threadIdx.x; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
+  constexpr int CW = W <= 2 ? W : 1;
+  __shared__ __align__(16) uint32_t cache_mem[gx::kBlock / 32][(1 << kBatchCacheLog2) * CW];
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const Group<G> g;
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
+  WarpCache cache{W <= 2 ? cache_mem[threadIdx.x >> 5] : nullptr, (1u << kBatchCacheLog2) - 1u};
+  int cached_net = -1;
   const unsigned long long total = a.prefix[a.n];
   constexpr int K = PerLane<G>::K;
   while (true) {
@@ -192,6 +202,11 @@ __global__ void __launch_bounds__(gx::kBlock) batch_expand_kernel(const BatchArg
       else hi = mid - 1;
     }
     BNet& b = a.nets[lo];
+    if (W <= 2 && lo != cached_net) {  // the cache holds one network's vectors at a time
+      for (uint32_t i = lane; i < (1u << kBatchCacheLog2) * CW; i += 32) cache_mem[threadIdx.x >> 5][i] = 0u;
+      __syncwarp();
+      cached_net = lo;
+    }
     const uint32_t* t = b.blob;
     const NetBlobLayout L = b.lay;
     const Target tg{b.table, b.log2nb, a.rounds, &b.next_end, b.frontier, b.fmask, b.cur_begin};
@@ -230,7 +245,7 @@ __global__ void __launch_bounds__(gx::kBlock) batch_expand_kernel(const BatchArg
             for (int w = 0; w < W; ++w) s[k][w] = 0;
           }
         }
-        insert_lanes<W, B, G, K>(tg, muls, g, has, s, probes, err, st);
+        insert_lanes<W, B, G, K>(tg, muls, g, has, s, probes, err, st, cache);
       }
     }
     st.flush<W>(tg, err);
