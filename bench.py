@@ -113,8 +113,9 @@ def measured_peaks() -> dict:
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured", sm_max_mhz=d.get("sm_max_mhz"))
-    return dict(hbm_gbs=6800.0, source="fallback", sm_max_mhz=2070.0)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured", sm_max_mhz=d.get("sm_max_mhz"),
+                    bf16_tflops_sustained=d.get("bf16_tflops_sustained"))
+    return dict(hbm_gbs=6800.0, source="fallback", sm_max_mhz=2070.0, bf16_tflops_sustained=1700.0)
 
 
 class ClockSampler:
@@ -349,16 +350,57 @@ def guided_part(torch, gx, inputs, guide) -> dict:
             del ws
             torch.cuda.empty_cache()
 
-    rows = []
-    for seed, n, k in ((1, 12, 2), (0, 13, 2), (1, 14, 2), (2, 16, 3)):
-        net = inputs.planted_network(seed, n, n_traps=k)
-        rows.append({"network": net.name, "processes": n, "planted_deadlocks": k,
-                     "guided": guided(net, params), "untrained": guided(net, untrained), "bfs": bfs(net)})
+    # five seeds per size; BFS where its table fits (at 16 processes it does not in 24 GiB)
+    rows, summary = [], []
+    for n, k in ((12, 2), (13, 2), (14, 2), (16, 3)):
+        per = []
+        for seed in range(5):
+            net = inputs.planted_network(seed, n, n_traps=k)
+            per.append({"network": net.name, "guided": guided(net, params), "untrained": guided(net, untrained),
+                        "bfs": bfs(net) if n <= 14 else {"skipped": "table beyond 24 GiB"}})
+        rows.extend(per)
+
+        def med(arm, key):
+            v = sorted(r[arm][key] for r in per if r[arm].get("found"))
+            return v[len(v) // 2] if v else None
+
+        summary.append({"processes": n, "planted_deadlocks": k, "seeds": 5,
+                        **{f"{arm}_found": sum(1 for r in per if r[arm].get("found")) for arm in
+                           ("guided", "untrained", "bfs")},
+                        **{f"{arm}_median_{key}": med(arm, key) for arm in ("guided", "untrained", "bfs")
+                           for key in ("explored", "ms")}})
     lo = losses.cpu().numpy()
     return {"train": {"networks": len(train_nets), "examples": int(hist.shape[0]),
                       "label_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3), "steps": 1500,
                       "loss_first": round(float(lo[:10].mean()), 4), "loss_last": round(float(lo[-50:].mean()), 4)},
-            "instances": rows}
+            "scoring": scoring_rate(torch, gx, params),
+            "summary": summary, "instances": rows}
+
+
+def scoring_rate(torch, gx, params, n=1 << 22) -> dict:
+    """Throughput of the tensor-core scorer (gx_mlp_forward) on n random histograms,
+    timed with CUDA events on the launching stream; FLOPs are the two layers' products
+    (2 x (16 x 128 + 128 x 128) per state) plus the output dot product."""
+    hist = torch.randint(0, 4, (n, 16), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        gx.mlp_forward(params, hist)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(st)
+    for _ in range(reps):
+        gx.mlp_forward(params, hist)
+    e1.record(st)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3 / reps
+    flops = 2.0 * (16 * 128 + 128 * 128 + 128) * n
+    pk = measured_peaks()
+    peak = pk["bf16_tflops_sustained"]
+    tf = flops / sec / 1e12
+    return {"states": n, "ms": round(sec * 1e3, 3), "states_per_s": round(n / sec, 1),
+            "tflops": round(tf, 2), "bf16_tflops_sustained": peak,
+            f"frac_of_{pk['source']}": round(tf / peak, 4) if peak else None,
+            "note": "each call synchronises; the scorer is bound by its CUDA-core epilogues, not the MMAs"}
 
 
 def STATUS(e) -> str:

@@ -231,11 +231,13 @@ gx_status gx_set_digest(gx_net* net, void* workspace, uint64_t workspace_bytes, 
  * Scoring network: x = hist / 16 where hist[i] = number of processes whose
  * local state is i (the one-hot local states summed over processes; networks
  * used with it have at most 16 local states per process), then
- * h1 = relu(W1 x + b1) (128 x 16), h2 = relu(W2 h1 + b2) (128 x 128),
+ * h1 = bf16(relu(W1 x + b1)) (128 x 16), h2 = relu(W2 h1 + b2) (128 x 128),
  * y = w3 . h2 + b3, trained to predict distance-to-deadlock / max_dist.  The
  * parameters are one FP32 vector W1 | b1 | W2 | b2 | w3 | b3 (GX_MLP_PARAMS
  * floats, device memory); every kernel uses the weights rounded to BF16
- * (round to nearest even) and accumulates in FP32.
+ * (round to nearest even), so each layer is a BF16 x BF16 product (x is exact
+ * in BF16, h1 is rounded) accumulated in FP32.  Scoring (gx_mlp_forward and
+ * the guided search) runs on the tensor cores, 128 states per tile.
  * ---------------------------------------------------------------------------------------- */
 #define GX_MLP_IN 16
 #define GX_MLP_HIDDEN 128
@@ -261,7 +263,9 @@ gx_status gx_training_set(gx_net* net, void* workspace, uint64_t workspace_bytes
  * uniform in +-1/sqrt(fan_in) from a splitmix64 stream, biases 0. */
 gx_status gx_mlp_init(float* params, uint64_t seed, void* stream);
 
-/* Scores of n examples (hist: device, 16 uint8 each) into out (device, n floats). */
+/* Scores of n examples (hist: device, 16 uint8 each, row-major) into out
+ * (device, n floats), on the tensor cores.  Synchronises `stream`.
+ * GX_ERR_SPIN_LIMIT if a wait for a tensor-core product timed out. */
 gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, float* out, void* stream);
 
 /* Gradient of the mean squared error over n examples at params (grad: device,

@@ -3,12 +3,14 @@
 The network (no counterpart in the paper): x = hist / 16, h1 = relu(W1 x + b1),
 h2 = relu(W2 h1 + b2), y = w3 . h2 + b3, loss = mean (y - label)^2, with the
 parameter vector laid out W1 (128 x 16) | b1 | W2 (128 x 128) | b2 | w3 | b3.
-With bf16=True the weights W1, W2, w3 are first rounded to bfloat16 (the
-upper 16 bits of the IEEE binary32 pattern, round to nearest, ties to even),
-as the GPU does; everything else is float64.  Gradients are taken with respect
-to the unrounded parameters through the rounded weights (the rounding itself
-passes gradients unchanged), which is what an optimiser on FP32 master
-weights sees.
+With bf16=True both factors of every weight product are bfloat16 (the upper
+16 bits of the IEEE binary32 pattern, round to nearest, ties to even), as on
+the tensor cores: the weights W1, W2, w3 are rounded, x is exact, and h1 is
+rounded (from its binary32 value) before it enters the second layer.
+Everything else is float64.  Gradients are taken with respect to the
+unrounded parameters through the rounded weights and activations (each
+rounding passes gradients unchanged), which is what an optimiser on FP32
+master weights sees.
 """
 import numpy as np
 
@@ -44,11 +46,16 @@ def _weights(p, bf16):
     return f(W1), f(b1), f(W2), f(b2), f(w3), float(b3)
 
 
+def _act(z, bf16):
+    """Layer input as the next product sees it: bfloat16 of its binary32 value."""
+    return bf16_round(np.asarray(z, dtype=np.float32)).astype(np.float64) if bf16 else z
+
+
 def forward(p, hist, bf16=True):
     W1, b1, W2, b2, w3, b3 = _weights(p, bf16)
     x = np.asarray(hist, dtype=np.float64) / 16.0
     a1 = x @ W1.T + b1
-    z1 = np.maximum(a1, 0)
+    z1 = _act(np.maximum(a1, 0), bf16)
     a2 = z1 @ W2.T + b2
     z2 = np.maximum(a2, 0)
     return z2 @ w3 + b3
@@ -60,7 +67,7 @@ def loss_and_grad(p, hist, label, bf16=True):
     t = np.asarray(label, dtype=np.float64)
     n = len(t)
     a1 = x @ W1.T + b1
-    z1 = np.maximum(a1, 0)
+    z1 = _act(np.maximum(a1, 0), bf16)
     a2 = z1 @ W2.T + b2
     z2 = np.maximum(a2, 0)
     y = z2 @ w3 + b3

@@ -10,13 +10,16 @@
 // processes' local states and the capped, normalised distance.
 //
 // Guided search (gx_find_deadlocks, GX_DL_GUIDED): open states live in
-// priority bins (stacks) by score; each iteration one CTA pops up to
-// guided_batch states from the best non-empty bin, then a persistent kernel
-// expands them: it logs each (state, parent log index), detects deadlocks,
-// find-or-puts every successor and scores each new one with the MLP (warp-
-// cooperative, BF16 weights in shared memory, FP32 accumulation) before
-// pushing it to its bin.  Every state is pushed once and popped once, so the
-// search ends either at a deadlock or after the whole state space.
+// priority bins (stacks) by score.  Each iteration:
+//   * one CTA pops up to guided_batch states from the best non-empty bin;
+//   * a persistent kernel expands them: it logs each (state, parent log
+//     index), detects deadlocks, find-or-puts every successor and appends
+//     each new one, with its local-state histogram, to a pending buffer;
+//   * the scoring kernel runs the MLP on the pending states, 128 per tile, on
+//     the tensor cores (tcgen05, BF16 operands, FP32 accumulation in TMEM;
+//     gx_tc.cuh) and pushes each state to the bin of its score.
+// Every state is pushed once and popped once, so the search ends either at a
+// deadlock or after the whole state space.
 
 #include <algorithm>
 #include <cstring>
@@ -26,6 +29,7 @@
 #include <cuda_bf16.h>
 
 #include "gx_kernels.cuh"
+#include "gx_tc.cuh"
 
 namespace gx {
 
@@ -40,6 +44,7 @@ struct GuidedCtl {
   unsigned int error, done;
   unsigned long long dl_count;
   unsigned long long claim;
+  unsigned long long pending;    // new states appended by the current iteration's expansion
 };
 
 struct GuidedArgs {
@@ -61,10 +66,13 @@ struct GuidedArgs {
   uint32_t* log;                  // [log_cap] entries
   uint64_t log_cap;
   const float* params;            // MLP, FP32 (rounded to BF16 when staged)
+  uint4* pend_hist;               // [pend_cap] local-state histograms of new states
+  uint32_t* pend;                 // [pend_cap] entries of E words (vector, parent)
+  uint64_t pend_cap;
   uint32_t init_vec[4];
 };
 
-constexpr unsigned int ERR_BINS = 16u, ERR_LOG = 32u, ERR_WIDE = 64u;
+constexpr unsigned int ERR_BINS = 16u, ERR_LOG = 32u, ERR_WIDE = 64u, ERR_PENDING = 128u;
 
 }  // namespace gx
 
@@ -73,10 +81,6 @@ namespace gxd {
 using gx::GuidedArgs;
 using gx::GuidedCtl;
 
-constexpr int MH = GX_MLP_HIDDEN;
-constexpr int MI = GX_MLP_IN;
-constexpr int LD1 = MI + 1;  // padded rows in shared memory (no bank conflicts)
-constexpr int LD2 = MH + 1;
 
 // Slot index of v in the table, or -1 when v is not stored.  Slots of a
 // bucket fill in order and are never freed, so an empty slot ends the search.
@@ -207,76 +211,6 @@ __global__ void __launch_bounds__(gx::kBlock) label_gather_kernel(const uint32_t
 
 // ---- guided search
 
-// MLP weights staged in shared memory (BF16-rounded, held as FP32).
-struct MlpSmem {
-  float* W1;  // [MH][LD1]
-  float* b1;  // [MH]
-  float* W2;  // [MH][LD2]
-  float* b2;  // [MH]
-  float* w3;  // [MH]
-  float b3;
-};
-
-__device__ __forceinline__ float bf16r(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
-
-__device__ __forceinline__ MlpSmem stage_mlp(float* sm, const float* p) {
-  MlpSmem m;
-  m.W1 = sm;
-  m.b1 = m.W1 + MH * LD1;
-  m.W2 = m.b1 + MH;
-  m.b2 = m.W2 + MH * LD2;
-  m.w3 = m.b2 + MH;
-  const float* pW1 = p;
-  const float* pb1 = pW1 + MH * MI;
-  const float* pW2 = pb1 + MH;
-  const float* pb2 = pW2 + MH * MH;
-  const float* pw3 = pb2 + MH;
-  for (int i = threadIdx.x; i < MH * MI; i += blockDim.x) m.W1[(i / MI) * LD1 + i % MI] = bf16r(pW1[i]);
-  for (int i = threadIdx.x; i < MH * MH; i += blockDim.x) m.W2[(i / MH) * LD2 + i % MH] = bf16r(pW2[i]);
-  for (int i = threadIdx.x; i < MH; i += blockDim.x) {
-    m.b1[i] = pb1[i];
-    m.b2[i] = pb2[i];
-    m.w3[i] = bf16r(pw3[i]);
-  }
-  m.b3 = pw3[MH];
-  return m;
-}
-
-constexpr size_t kMlpSmemFloats = MH * LD1 + MH + MH * LD2 + MH + MH;
-
-// Score of the state whose histogram words hw (identical in all lanes) are
-// given; all 32 lanes cooperate (lane owns hidden units lane + 32q).
-__device__ __forceinline__ float warp_score(const MlpSmem& m, const uint32_t (&hw)[4], float* h1) {
-  const int lane = threadIdx.x & 31;
-  float x[MI];
-#pragma unroll
-  for (int i = 0; i < MI; ++i) x[i] = (float)((hw[i >> 2] >> ((i & 3) * 8)) & 0xFFu) * (1.0f / 16.0f);
-  float a1[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int k = lane + 32 * q;
-    float a = m.b1[k];
-#pragma unroll
-    for (int i = 0; i < MI; ++i) a += m.W1[k * LD1 + i] * x[i];
-    a1[q] = fmaxf(a, 0.f);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int q = 0; q < 4; ++q) h1[lane + 32 * q] = a1[q];
-  __syncwarp();
-  float part = 0.f;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int k = lane + 32 * q;
-    float a = m.b2[k];
-    for (int j = 0; j < MH; ++j) a += m.W2[k * LD2 + j] * h1[j];
-    part += m.w3[k] * fmaxf(a, 0.f);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULLMASK, part, o);
-  return part + m.b3;
-}
-
 template <int W>
 __device__ __forceinline__ void push_bin(const GuidedArgs& a, float score, const uint32_t (&v)[W], uint32_t parent,
                                          uint32_t& err) {
@@ -299,29 +233,26 @@ __device__ __forceinline__ void push_bin(const GuidedArgs& a, float score, const
   err |= gx::ERR_BINS;
 }
 
+// The initial state: into the table and the first bin (as the only open
+// state its score does not matter).
 template <int W, int B>
-__global__ void __launch_bounds__(gx::kBlock) guided_init_kernel(const GuidedArgs a) {
-  extern __shared__ __align__(16) float gsm[];
+__global__ void __launch_bounds__(32) guided_init_kernel(const GuidedArgs a) {
   __shared__ uint64_t muls[kMaxRounds];
-  __shared__ float h1buf[MH];
   for (int i = threadIdx.x; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
-  const MlpSmem m = stage_mlp(gsm, a.params);
-  __syncthreads();
-  if (threadIdx.x >= 32) return;
+  __syncwarp();
+  if (threadIdx.x != 0) return;
   uint32_t v[W];
 #pragma unroll
   for (int w = 0; w < W; ++w) v[w] = a.init_vec[w];
   uint32_t hw[4], bad = 0;
   local_hist<W>(a.blob, a.lay, v, hw, bad);
-  const float y = warp_score(m, hw, h1buf);
-  if (threadIdx.x != 0) return;
   const Group<1> g;
   uint32_t probes = 0, err = bad ? gx::ERR_WIDE : 0u;
   const int r = find_or_put<W, B, 1>(a.table, a.log2nb, a.rounds, muls, v, g, probes);
   if (r != FOP_INSERTED) err |= gx::ERR_TABLE_FULL;
   else {
     a.ctl->inserted = 1;
-    push_bin<W>(a, y, v, 0xFFFFFFFFu, err);
+    push_bin<W>(a, 0.f, v, 0xFFFFFFFFu, err);
   }
   if (err) atomicOr(&a.ctl->error, err);
 }
@@ -337,6 +268,7 @@ __global__ void __launch_bounds__(1024) guided_select_kernel(const GuidedArgs a)
     GuidedCtl& c = *a.ctl;
     c.batch_n = 0;
     c.claim = 0;
+    c.pending = 0;
     if (c.found == ~0ull && !c.error) {
       for (int b = 0; b < a.nbins; ++b) {
         unsigned long long cnt = a.bin_count[b];
@@ -374,21 +306,18 @@ __global__ void __launch_bounds__(1024) guided_select_kernel(const GuidedArgs a)
 template <int W, int B>
 __global__ void __launch_bounds__(gx::kBlock) guided_expand_kernel(const GuidedArgs a) {
   constexpr int E = W + 1;
-  extern __shared__ __align__(16) float gsm[];
+  extern __shared__ __align__(16) uint32_t gsm[];
   __shared__ uint64_t muls[kMaxRounds];
-  __shared__ float h1buf[gx::kBlock / 32][MH];
   for (int i = threadIdx.x; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
-  const MlpSmem m = stage_mlp(gsm, a.params);
   const uint32_t* t = a.blob;
   if (a.stage) {
-    uint32_t* s_tab = reinterpret_cast<uint32_t*>(gsm + kMlpSmemFloats);
+    uint32_t* s_tab = gsm;
     for (uint32_t i = threadIdx.x; i < a.blob_words; i += blockDim.x) s_tab[i] = a.blob[i];
     t = s_tab;
   }
   __syncthreads();
   const NetBlobLayout& L = a.lay;
   const int lane = threadIdx.x & 31;
-  float* h1 = h1buf[threadIdx.x >> 5];
   const Group<1> g;
   const unsigned long long n = a.ctl->batch_n;
   const unsigned long long log_base = a.ctl->log_base;
@@ -439,16 +368,24 @@ __global__ void __launch_bounds__(gx::kBlock) guided_expand_kernel(const GuidedA
       uint32_t hw[4] = {0, 0, 0, 0}, bad = 0;
       if (inserted) local_hist<W>(t, L, s, hw, bad);
       if (bad) err |= gx::ERR_WIDE;
-      uint32_t im = __ballot_sync(FULLMASK, inserted);
+      const uint32_t im = __ballot_sync(FULLMASK, inserted);
       ins += inserted ? 1u : 0u;
-      while (im) {  // score the new states one at a time, all lanes together
-        const int src = __ffs(im) - 1;
-        im &= im - 1;
-        uint32_t h[4];
+      if (im) {  // append the new states to the pending buffer, one atomic per warp
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&a.ctl->pending, (unsigned long long)__popc(im));
+        base = __shfl_sync(FULLMASK, base, 0);
+        if (inserted) {
+          const unsigned long long pos = base + __popc(im & ((1u << lane) - 1u));
+          if (pos < a.pend_cap) {
+            a.pend_hist[pos] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+            uint32_t* e = a.pend + pos * E;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) h[q] = __shfl_sync(FULLMASK, hw[q], src);
-        const float y = warp_score(m, h, h1);
-        if (lane == src) push_bin<W>(a, y, s, (uint32_t)li, err);
+            for (int w = 0; w < W; ++w) e[w] = s[w];
+            e[W] = (uint32_t)li;
+          } else {
+            err |= gx::ERR_PENDING;
+          }
+        }
       }
     }
   }
@@ -462,6 +399,46 @@ __global__ void __launch_bounds__(gx::kBlock) guided_expand_kernel(const GuidedA
     if (pr) atomicAdd(&a.ctl->probes, pr);
     if (err) atomicOr(&a.ctl->error, err);
   }
+}
+
+// Score the pending states on the tensor cores and push each to its bin.
+// 128 threads; persistent over tiles of 128 states.
+template <int W>
+__global__ void __launch_bounds__(gxt::kRows) guided_score_kernel(const GuidedArgs a) {
+  constexpr int E = W + 1;
+  extern __shared__ __align__(16) uint8_t tsm[];
+  unsigned long long n = a.ctl->pending;
+  if (n > a.pend_cap) n = a.pend_cap;  // the expansion reported the overflow
+  const unsigned long long tiles = (n + gxt::kRows - 1) / gxt::kRows;
+  if (blockIdx.x >= tiles) return;
+  gxt::TcScorer sc = gxt::tc_setup(tsm, a.params);
+  uint32_t err = 0;
+  for (unsigned long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const unsigned long long row = tile * gxt::kRows + threadIdx.x;
+    const bool valid = row < n;
+    uint32_t hw[4] = {0, 0, 0, 0};
+    if (valid) {
+      const uint4 q = a.pend_hist[row];
+      hw[0] = q.x;
+      hw[1] = q.y;
+      hw[2] = q.z;
+      hw[3] = q.w;
+    }
+    float y = 0.f;
+    if (!gxt::tc_score_tile(sc, hw, y)) {
+      err |= gx::ERR_SPIN;
+      break;
+    }
+    if (valid) {
+      uint32_t v[W];
+      const uint32_t* e = a.pend + row * E;
+#pragma unroll
+      for (int w = 0; w < W; ++w) v[w] = e[w];
+      push_bin<W>(a, y, v, e[W], err);
+    }
+  }
+  gxt::tc_teardown(sc);
+  if (err) atomicOr(&a.ctl->error, err);
 }
 
 }  // namespace gxd
@@ -484,13 +461,15 @@ struct GKernels {
   const void* init;
   const void* select;
   const void* expand;
+  const void* score;
 };
 
 template <int W, int B>
 GKernels gk() {
   return GKernels{&gxd::label_sweep_kernel<W, B>, reinterpret_cast<const void*>(&gxd::guided_init_kernel<W, B>),
                   reinterpret_cast<const void*>(&gxd::guided_select_kernel<W>),
-                  reinterpret_cast<const void*>(&gxd::guided_expand_kernel<W, B>)};
+                  reinterpret_cast<const void*>(&gxd::guided_expand_kernel<W, B>),
+                  reinterpret_cast<const void*>(&gxd::guided_score_kernel<W>)};
 }
 
 bool gk_lookup(int W, int B, GKernels& k) {
@@ -513,8 +492,8 @@ struct GPlan {
   int W, B, rounds, nbins;
   float scale;
   uint32_t batch_cap;
-  uint64_t nb, slots, bin_cap, log_cap;
-  uint64_t off_ctl, off_blob, off_bincnt, off_table, off_bins, off_batch, off_log, total;
+  uint64_t nb, slots, bin_cap, log_cap, pend_cap;
+  uint64_t off_ctl, off_blob, off_bincnt, off_table, off_bins, off_batch, off_log, off_pend_hist, off_pend, total;
   GKernels k;
 };
 
@@ -539,6 +518,9 @@ gx_status guided_plan(const Net& net, const gx_explore_opts* o, GPlan& P) {
   P.slots = nb * (uint64_t)(P.B / P.W);
   P.log_cap = P.slots;                                   // every state is expanded at most once
   P.bin_cap = std::max<uint64_t>(P.batch_cap, (P.slots + P.nbins - 1) / P.nbins + 1);
+  // one iteration inserts at most batch x (successors of a state) states, and
+  // never more than the table holds
+  P.pend_cap = std::min<uint64_t>(P.slots, (uint64_t)P.batch_cap * std::max<uint64_t>(net.max_succ, 1));
   const uint64_t E = (uint64_t)P.W + 1;
   uint64_t off = 0;
   P.off_ctl = off;
@@ -555,6 +537,10 @@ gx_status guided_plan(const Net& net, const gx_explore_opts* o, GPlan& P) {
   off = a256(off + 4ull * E * P.batch_cap);
   P.off_log = off;
   off = a256(off + 4ull * E * P.log_cap);
+  P.off_pend_hist = off;
+  off = a256(off + 16ull * P.pend_cap);
+  P.off_pend = off;
+  off = a256(off + 4ull * E * P.pend_cap);
   P.total = off;
   return GX_OK;
 }
@@ -597,16 +583,21 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
   a.log = reinterpret_cast<uint32_t*>(base + P.off_log);
   a.log_cap = P.log_cap;
   a.params = h->guided_params;
+  a.pend_hist = reinterpret_cast<uint4*>(base + P.off_pend_hist);
+  a.pend = reinterpret_cast<uint32_t*>(base + P.off_pend);
+  a.pend_cap = P.pend_cap;
   for (int w = 0; w < 4; ++w) a.init_vec[w] = net.init_vec[w];
-  const size_t mlp_bytes = sizeof(float) * gxd::kMlpSmemFloats;
   const size_t blob_bytes = 4ull * net.blob.size();
-  a.stage = (mlp_bytes + blob_bytes <= (size_t)optin - 32 * 1024) ? 1 : 0;
-  const size_t smem = mlp_bytes + (a.stage ? blob_bytes : 0);
+  a.stage = (blob_bytes <= (size_t)optin - 32 * 1024) ? 1 : 0;
+  const size_t smem = a.stage ? blob_bytes : 0;
   GG_CUDA(cudaFuncSetAttribute(P.k.expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  GG_CUDA(cudaFuncSetAttribute(P.k.init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mlp_bytes));
-  int per_sm = 0;
+  GG_CUDA(cudaFuncSetAttribute(P.k.score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gxt::kTcSmemBytes));
+  int per_sm = 0, score_per_sm = 0;
   GG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.k.expand, kBlock, smem));
+  GG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&score_per_sm, P.k.score, gxt::kRows, gxt::kTcSmemBytes));
   const int grid = sms * std::max(per_sm, 1);
+  // each scoring CTA holds 128 of an SM's 512 TMEM columns
+  const int score_grid = sms * std::min(std::max(score_per_sm, 1), 4);
 
   cudaEvent_t e0, e1;
   GG_CUDA(cudaEventCreate(&e0));
@@ -619,12 +610,13 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
   GG_CUDA(cudaMemsetAsync(a.bin_count, 0, 8ull * P.nbins, st));
   GG_CUDA(cudaMemsetAsync(a.table, 0, 4ull * P.B * P.nb, st));
   void* args[] = {&a};
-  GG_CUDA(cudaLaunchKernel(P.k.init, dim3(1), dim3(kBlock), args, mlp_bytes, st));
+  GG_CUDA(cudaLaunchKernel(P.k.init, dim3(1), dim3(32), args, 0, st));
   GuidedCtl hc{};
   uint64_t iters = 0;
   while (true) {
     GG_CUDA(cudaLaunchKernel(P.k.select, dim3(1), dim3(1024), args, 0, st));
     GG_CUDA(cudaLaunchKernel(P.k.expand, dim3(grid), dim3(kBlock), args, smem, st));
+    GG_CUDA(cudaLaunchKernel(P.k.score, dim3(score_grid), dim3(gxt::kRows), args, gxt::kTcSmemBytes, st));
     GG_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
     GG_CUDA(cudaStreamSynchronize(st));
     ++iters;
@@ -684,6 +676,8 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
   else if (hc.error & ERR_BINS) rs = fail(GX_ERR_FRONTIER_OVERFLOW, "priority bins full");
   else if (hc.error & ERR_LOG) rs = fail(GX_ERR_OOM, "log of expanded states full");
   else if (hc.error & ERR_WIDE) rs = fail(GX_ERR_INVALID, "a local state index is 16 or more");
+  else if (hc.error & ERR_PENDING) rs = fail(GX_ERR_FRONTIER_OVERFLOW, "pending buffer of new states full");
+  else if (hc.error & ERR_SPIN) rs = fail(GX_ERR_SPIN_LIMIT, "tensor-core scoring timed out waiting for an MMA");
   S.status = (uint32_t)rs;
   return rs;
 }

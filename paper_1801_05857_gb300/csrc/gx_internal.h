@@ -42,6 +42,10 @@ struct Net {
   std::vector<uint32_t> n_states, initial;
   std::vector<uint32_t> field_word, field_shift, field_bits;
   uint32_t max_rule_parts = 0;
+  // upper bound on the successors of any state: per process the most local
+  // edges from one state, plus per rule the product over its participants of
+  // the most matching edges from one state (capped at 2^40)
+  uint64_t max_succ = 0;
   std::vector<uint32_t> blob;
   NetBlobLayout lay{};
   uint32_t init_vec[kMaxWords] = {0, 0, 0, 0};

@@ -3,7 +3,7 @@
 // from the histogram of its processes' local states.
 //
 //   x  = hist / 16                      (hist[i] = processes in local state i, i < 16)
-//   h1 = relu(W1 x + b1)                W1: 128 x 16
+//   h1 = bf16(relu(W1 x + b1))          W1: 128 x 16
 //   h2 = relu(W2 h1 + b2)               W2: 128 x 128
 //   y  = w3 . h2 + b3
 //
@@ -11,11 +11,17 @@
 // input: the first layer's weights are shared by all processes, which is
 // what lets a network trained on small instances score states of larger ones.
 // Weights are used in BF16 (rounded to nearest even from FP32 master copies
-// that the optimiser updates); every product is accumulated in FP32.
+// that the optimiser updates), and so is each layer's input (x is exact in
+// BF16; h1 is rounded), so that both layers are BF16 x BF16 products with
+// FP32 accumulation -- the operand types of the tensor cores.  Inference
+// (gx_mlp_forward, and the guided search's scoring) runs on the tensor cores
+// (gx_tc.cuh); the gradient kernel below computes the same network on the
+// CUDA cores.
 //
 // Parameter vector (FP32, GX_MLP_PARAMS floats): W1 | b1 | W2 | b2 | w3 | b3.
 // Loss: mean over the batch of (y - label)^2.
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -24,6 +30,7 @@
 #include <cuda_bf16.h>
 
 #include "gx_kernels.h"
+#include "gx_tc.cuh"
 
 namespace gxm {
 
@@ -91,7 +98,7 @@ __global__ void __launch_bounds__(H) mlp_kernel(const float* __restrict__ p, con
     float a1 = b1;
 #pragma unroll
     for (int i = 0; i < IN; ++i) a1 += w1[i] * x[i];
-    const float z1 = fmaxf(a1, 0.f);
+    const float z1 = bf(fmaxf(a1, 0.f));
     h1[k] = z1;
     __syncthreads();
     float a2 = b2;
@@ -131,6 +138,34 @@ __global__ void __launch_bounds__(H) mlp_kernel(const float* __restrict__ p, con
     atomicAdd(&g[OFF_B3], gb3);
     atomicAdd(loss, lsum);
   }
+}
+
+// Inference on the tensor cores: persistent over tiles of 128 examples.
+__device__ unsigned int g_tc_error;
+
+__global__ void __launch_bounds__(gxt::kRows) mlp_tc_forward_kernel(const float* __restrict__ p,
+                                                                     const uint8_t* __restrict__ hist, uint64_t n,
+                                                                     float* __restrict__ out) {
+  extern __shared__ __align__(16) uint8_t tsm[];
+  const uint64_t tiles = (n + gxt::kRows - 1) / gxt::kRows;
+  if (blockIdx.x >= tiles) return;
+  gxt::TcScorer sc = gxt::tc_setup(tsm, p);
+  for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const uint64_t row = tile * gxt::kRows + threadIdx.x;
+    uint32_t hw[4] = {0, 0, 0, 0};
+    if (row < n) {
+      const uint8_t* h = hist + row * IN;
+#pragma unroll
+      for (int i = 0; i < IN; ++i) hw[i >> 2] |= (uint32_t)h[i] << ((i & 3) * 8);
+    }
+    float y = 0.f;
+    if (!gxt::tc_score_tile(sc, hw, y)) {
+      if (threadIdx.x == 0) atomicOr(&g_tc_error, 1u);
+      break;
+    }
+    if (row < n) out[row] = y;
+  }
+  gxt::tc_teardown(sc);
 }
 
 // Adam (Kingma & Ba 2015) on the FP32 master parameters; clears the gradient.
@@ -175,8 +210,8 @@ gx_status set_smem() {
   if (done) return GX_OK;
   GM_CUDA(cudaFuncSetAttribute(gxm::mlp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)gxm::smem_bytes(true)));
-  GM_CUDA(cudaFuncSetAttribute(gxm::mlp_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)gxm::smem_bytes(false)));
+  GM_CUDA(cudaFuncSetAttribute(gxm::mlp_tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)gxt::kTcSmemBytes));
   done = true;
   return GX_OK;
 }
@@ -217,10 +252,23 @@ gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, f
   if (n == 0) return GX_OK;
   gx_status s = set_smem();
   if (s != GX_OK) return s;
-  const uint64_t grid = (n + gxm::EPB - 1) / gxm::EPB;
-  gxm::mlp_kernel<false><<<(unsigned)grid, gxm::H, gxm::smem_bytes(false), static_cast<cudaStream_t>(stream)>>>(
-      params, hist, nullptr, n, nullptr, 0.f, out, nullptr, nullptr);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0, per_sm = 0;
+  GM_CUDA(cudaGetDevice(&dev));
+  GM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  GM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gxm::mlp_tc_forward_kernel, gxt::kRows,
+                                                        gxt::kTcSmemBytes));
+  // each CTA holds 128 of an SM's 512 TMEM columns
+  const uint64_t tiles = (n + gxt::kRows - 1) / gxt::kRows;
+  const uint64_t grid = std::min<uint64_t>(tiles, (uint64_t)sms * std::min(std::max(per_sm, 1), 4));
+  const unsigned int zero = 0;
+  GM_CUDA(cudaMemcpyToSymbolAsync(gxm::g_tc_error, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st));
+  gxm::mlp_tc_forward_kernel<<<(unsigned)grid, gxt::kRows, gxt::kTcSmemBytes, st>>>(params, hist, n, out);
   GM_CUDA(cudaGetLastError());
+  unsigned int err = 0;
+  GM_CUDA(cudaMemcpyFromSymbolAsync(&err, gxm::g_tc_error, sizeof(err), 0, cudaMemcpyDeviceToHost, st));
+  GM_CUDA(cudaStreamSynchronize(st));
+  if (err) return gx::fail(GX_ERR_SPIN_LIMIT, "tensor-core scoring timed out waiting for an MMA");
   return GX_OK;
 }
 

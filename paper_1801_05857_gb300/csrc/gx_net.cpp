@@ -16,6 +16,7 @@
 // interest) that the kernels stage into shared memory -- the role the paper
 // gives to texture memory (Sec. 3).
 
+#include <algorithm>
 #include <cstring>
 #include <set>
 #include <string>
@@ -166,6 +167,25 @@ static gx_status encode(const gx_net_desc* d, Net& net) {
     for (uint32_t j = 0; j < R.n_parts; ++j) rule_cls.push_back(find_class(R.proc[j], R.label[j]));
     rule_off.push_back((uint32_t)rule_cls.size());
   }
+  // --- successor bound (sizes buffers that hold one batch's new states)
+  std::vector<uint64_t> cls_maxdeg(classes.size(), 0);
+  for (size_t c = 0; c < classes.size(); ++c) {
+    const uint32_t ns = d->procs[classes[c].proc].n_states;
+    for (uint32_t s = 0; s < ns; ++s)
+      cls_maxdeg[c] = std::max<uint64_t>(cls_maxdeg[c], coff[cls_base[c] + s + 1] - coff[cls_base[c] + s]);
+  }
+  constexpr uint64_t kSuccCap = 1ull << 40;
+  uint64_t bound = 0;
+  for (uint32_t p = 0; p < n; ++p) bound += cls_maxdeg[p];
+  for (uint32_t r = 0; r < d->n_rules; ++r) {
+    uint64_t prod = 1;
+    for (uint32_t j = rule_off[r]; j < rule_off[r + 1]; ++j) {
+      const uint64_t m = cls_maxdeg[rule_cls[j]];
+      prod = (m && prod > kSuccCap / m) ? kSuccCap : prod * m;
+    }
+    bound = std::min(kSuccCap, bound + prod);
+  }
+  net.max_succ = bound;
   std::vector<uint32_t>& B = net.blob;
   B.clear();
   auto put = [&](const std::vector<uint32_t>& v) {

@@ -62,6 +62,30 @@ def test_mlp_forward_and_gradient_match_float64(cuda):
     assert np.max(np.abs(g - gr)) <= 1e-3 * np.max(np.abs(gr)) + 1e-7
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 4099, 152 * 4 * 128 * 2 + 77])
+def test_tensor_core_forward_tiles_match_float64(cuda, n):
+    """gx_mlp_forward scores 128 states per tile on the tensor cores; ragged
+    tails, a single state, and more tiles than CTAs (each CTA loops) must all
+    equal the float64 network with BF16 operands.  Rows 0 and 1 are the
+    extreme inputs: every process in local state 15, and all 16 processes in
+    state 0."""
+    import torch
+    p = torch.empty(gx.MLP_PARAMS, dtype=torch.float32, device="cuda")
+    gx.mlp_init(p, 7)
+    rng = np.random.default_rng(n)
+    hist_np = rng.multinomial(12, np.ones(16) / 16, size=n).astype(np.uint8)
+    hist_np[0] = 0
+    hist_np[0, 15] = 16
+    if n > 1:
+        hist_np[1] = 0
+        hist_np[1, 0] = 16
+    y = gx.mlp_forward(p, torch.from_numpy(hist_np).cuda()).cpu().numpy()
+    pick = np.unique(np.concatenate([np.arange(min(n, 300)), rng.integers(0, n, 700), [n - 1]]))
+    yr = omlp.forward(p.cpu().numpy(), hist_np[pick])
+    assert np.isfinite(y).all()
+    assert np.max(np.abs(y[pick] - yr)) < 1e-4
+
+
 def _trained(steps=600):
     nets = [inputs.planted_network(s, n, n_traps=1 + s % 4) for s in range(6) for n in (6, 7, 8)]
     hist, label = guide.collect_examples(nets, MAX_DIST)
@@ -86,10 +110,10 @@ def _replay(net, trace):
     assert len(oracle.successors(net, trace[-1])) == 0
 
 
-def _guided(net, params, **kw):
+def _guided(net, params, table_bytes=1 << 27, **kw):
     h = gx.load_network(net)
     gx.guided_set_weights(h, params)
-    o = gx.default_opts(table_bytes=1 << 27, hash_rounds=32, **kw)
+    o = gx.default_opts(table_bytes=table_bytes, hash_rounds=32, **kw)
     ws = gx.guided_alloc_workspace(h, o)
     n, found = gx.find_deadlocks(h, gx.GX_DL_GUIDED, o, ws)
     return h, n, found, gx.stats(h)
@@ -123,8 +147,8 @@ def test_trained_network_beats_untrained(cuda):
     untrained = torch.empty(gx.MLP_PARAMS, dtype=torch.float32, device="cuda")
     gx.mlp_init(untrained, 99)
     net = inputs.planted_network(21, 11, n_traps=2)
-    _, n1, _, s1 = _guided(net, params)
-    _, n2, _, s2 = _guided(net, untrained)
+    _, n1, _, s1 = _guided(net, params, table_bytes=1 << 29)
+    _, n2, _, s2 = _guided(net, untrained, table_bytes=1 << 29)
     assert n1 == 1 and n2 == 1
     assert s1["explored"] < s2["explored"]
 

@@ -278,3 +278,23 @@ def test_bf16_rounding_definition():
     assert r[3] == 1.0
     assert r[4] == -2.5 and r[5] == np.float32(3.140625)
     assert ((r.view(np.uint32) & 0xFFFF) == 0).all()
+
+
+def test_mlp_oracle_rounds_the_hidden_layer_input_to_bf16():
+    """Closed-form case: W1 = 0 and b1 = 1 + 2^-8 (a bfloat16 tie) make every
+    hidden unit 1 + 2^-8 before rounding.  W2 = I (first unit only), w3 = e0,
+    b2 = b3 = 0 pass the first unit to the output, so y is 1 exactly when the
+    second layer sees the rounded value (tie to even), and 1 + 2^-8 without
+    rounding.  A hidden unit of 1 + 3 * 2^-8 rounds up to 1 + 2^-6 instead."""
+    from oracle import mlp
+    for pre, want in ((1 + 2 ** -8, 1.0), (1 + 3 * 2 ** -8, 1 + 2 ** -6)):
+        p = np.zeros(mlp.NPARAM, dtype=np.float32)
+        o = mlp.H * mlp.IN
+        p[o:o + mlp.H] = pre                              # b1
+        o += mlp.H
+        p[o] = 1.0                                        # W2[0, 0]
+        o += mlp.H * mlp.H + mlp.H
+        p[o] = 1.0                                        # w3[0]
+        hist = np.array([[3] + [0] * 15, [0] * 15 + [16]])
+        assert (mlp.forward(p, hist) == want).all()
+        assert (mlp.forward(p, hist, bf16=False) == np.float64(np.float32(pre))).all()
