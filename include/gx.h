@@ -228,15 +228,17 @@ gx_status gx_set_digest(gx_net* net, void* workspace, uint64_t workspace_bytes, 
  * Learned guidance for deadlock search (no counterpart in the paper; the
  * exhaustive search it reorders is the one of Sec. 3).
  *
- * Scoring network: x = hist / 16 where hist[i] = number of processes whose
- * local state is i (the one-hot local states summed over processes; networks
- * used with it have at most 16 local states per process), then
+ * Scoring network: x = bf16(hist * (1 / n)) where hist[i] = number of
+ * processes whose local state is i and n = sum of hist (the one-hot local
+ * states averaged over processes, so the input has the same scale at every
+ * network size; networks used with it have at most 16 local states per
+ * process; an all-zero row gives x = 0), then
  * h1 = bf16(relu(W1 x + b1)) (128 x 16), h2 = relu(W2 h1 + b2) (128 x 128),
  * y = w3 . h2 + b3, trained to predict distance-to-deadlock / max_dist.  The
  * parameters are one FP32 vector W1 | b1 | W2 | b2 | w3 | b3 (GX_MLP_PARAMS
  * floats, device memory); every kernel uses the weights rounded to BF16
- * (round to nearest even), so each layer is a BF16 x BF16 product (x is exact
- * in BF16, h1 is rounded) accumulated in FP32.  Scoring (gx_mlp_forward and
+ * (round to nearest even), so each layer is a BF16 x BF16 product (x and h1
+ * are rounded from FP32) accumulated in FP32.  Scoring (gx_mlp_forward and
  * the guided search) runs on the tensor cores, 128 states per tile.
  * ---------------------------------------------------------------------------------------- */
 #define GX_MLP_IN 16

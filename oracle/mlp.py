@@ -1,12 +1,14 @@
 """FP64 reference of the scoring network of the guided search -- TEST INFRASTRUCTURE ONLY.
 
-The network (no counterpart in the paper): x = hist / 16, h1 = relu(W1 x + b1),
+The network (no counterpart in the paper): x = hist / n with n = sum(hist) the
+number of processes (x = 0 for an all-zero row), h1 = relu(W1 x + b1),
 h2 = relu(W2 h1 + b2), y = w3 . h2 + b3, loss = mean (y - label)^2, with the
 parameter vector laid out W1 (128 x 16) | b1 | W2 (128 x 128) | b2 | w3 | b3.
 With bf16=True both factors of every weight product are bfloat16 (the upper
 16 bits of the IEEE binary32 pattern, round to nearest, ties to even), as on
-the tensor cores: the weights W1, W2, w3 are rounded, x is exact, and h1 is
-rounded (from its binary32 value) before it enters the second layer.
+the tensor cores: the weights W1, W2, w3 are rounded, and so are x (from the
+binary32 product hist * (1 / n), both steps rounded to nearest in binary32)
+and h1 (from its binary32 value) before they enter their layers.
 Everything else is float64.  Gradients are taken with respect to the
 unrounded parameters through the rounded weights and activations (each
 rounding passes gradients unchanged), which is what an optimiser on FP32
@@ -51,9 +53,20 @@ def _act(z, bf16):
     return bf16_round(np.asarray(z, dtype=np.float32)).astype(np.float64) if bf16 else z
 
 
+def features(hist, bf16=True):
+    """x = hist / n, n = number of processes (row sum); 0 for an all-zero row."""
+    h = np.asarray(hist, dtype=np.float64)
+    n = h.sum(axis=1, keepdims=True)
+    if not bf16:
+        return np.divide(h, n, out=np.zeros_like(h), where=n > 0)
+    inv = np.zeros(n.shape, dtype=np.float32)
+    np.divide(np.float32(1), n.astype(np.float32), out=inv, where=n > 0)
+    return bf16_round(h.astype(np.float32) * inv).astype(np.float64)
+
+
 def forward(p, hist, bf16=True):
     W1, b1, W2, b2, w3, b3 = _weights(p, bf16)
-    x = np.asarray(hist, dtype=np.float64) / 16.0
+    x = features(hist, bf16)
     a1 = x @ W1.T + b1
     z1 = _act(np.maximum(a1, 0), bf16)
     a2 = z1 @ W2.T + b2
@@ -63,7 +76,7 @@ def forward(p, hist, bf16=True):
 
 def loss_and_grad(p, hist, label, bf16=True):
     W1, b1, W2, b2, w3, b3 = _weights(p, bf16)
-    x = np.asarray(hist, dtype=np.float64) / 16.0
+    x = features(hist, bf16)
     t = np.asarray(label, dtype=np.float64)
     n = len(t)
     a1 = x @ W1.T + b1

@@ -2,17 +2,19 @@
 // paper): a small MLP that predicts a state's distance to the nearest deadlock
 // from the histogram of its processes' local states.
 //
-//   x  = hist / 16                      (hist[i] = processes in local state i, i < 16)
+//   x  = bf16(hist / n)                 (hist[i] = processes in local state i, i < 16;
+//                                        n = sum of hist = the network's processes)
 //   h1 = bf16(relu(W1 x + b1))          W1: 128 x 16
 //   h2 = relu(W2 h1 + b2)               W2: 128 x 128
 //   y  = w3 . h2 + b3
 //
-// The one-hot local state of each process, summed over processes, is the
-// input: the first layer's weights are shared by all processes, which is
-// what lets a network trained on small instances score states of larger ones.
+// The one-hot local state of each process, averaged over processes, is the
+// input: the first layer's weights are shared by all processes, and the
+// input has the same scale at every network size, which is what lets a
+// network trained on small instances score states of larger ones.
 // Weights are used in BF16 (rounded to nearest even from FP32 master copies
-// that the optimiser updates), and so is each layer's input (x is exact in
-// BF16; h1 is rounded), so that both layers are BF16 x BF16 products with
+// that the optimiser updates), and so is each layer's input (x and h1 are
+// rounded from FP32), so that both layers are BF16 x BF16 products with
 // FP32 accumulation -- the operand types of the tensor cores.  Inference
 // (gx_mlp_forward, and the guided search's scoring) runs on the tensor cores
 // (gx_tc.cuh); the gradient kernel below computes the same network on the
@@ -93,7 +95,13 @@ __global__ void __launch_bounds__(H) mlp_kernel(const float* __restrict__ p, con
     const uint64_t slot = (uint64_t)blockIdx.x * EPB + e;
     if (slot >= n) break;  // uniform in the block
     const uint64_t ex = index ? index[slot] : slot;
-    if (k < IN) x[k] = hist[ex * IN + k] * (1.0f / 16.0f);
+    if (k < 32) {  // warp 0: x = bf16(hist * (1 / number of processes))
+      const uint32_t h = k < IN ? hist[ex * IN + k] : 0u;
+      uint32_t n = h;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
+      if (k < IN) x[k] = n ? bf((float)h * (1.0f / (float)n)) : 0.f;
+    }
     __syncthreads();
     float a1 = b1;
 #pragma unroll

@@ -6,7 +6,7 @@
 // also TMEM lane t of the M = 128 accumulator, so every epilogue is
 // thread-local:
 //
-//   X  (128 x 16 BF16)  = hist / 16                    (exact in BF16)
+//   X  (128 x 16 BF16)  = bf16(hist / sum(hist))      (fraction of processes per local state)
 //   A1 = X W1^T         -> TMEM columns [0, 128)      one MMA, K = 16
 //   H  (128 x 128 BF16) = bf16(relu(A1 + b1))          written to shared memory
 //   A2 = H W2^T         -> TMEM columns [0, 128)      eight MMAs, K = 16 each
@@ -133,6 +133,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&b);
 }
 
+// 1 / (number of processes) for a histogram packed 4 counts per word; 0 when empty.
+__device__ __forceinline__ float feature_scale(const uint32_t (&hw)[4]) {
+  uint32_t n = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) n += (hw[i] & 0xFFu) + ((hw[i] >> 8) & 0xFFu) + ((hw[i] >> 16) & 0xFFu) + (hw[i] >> 24);
+  return n ? 1.0f / (float)n : 0.f;
+}
+
 // Byte offset of element (row, k) in a no-swizzle K-major operand with KG
 // K groups of 8 elements.
 __host__ __device__ constexpr uint32_t core_offset(uint32_t row, uint32_t k, uint32_t KG) {
@@ -240,14 +248,16 @@ __device__ __forceinline__ bool tc_score_tile(TcScorer& sc, const uint32_t (&hw)
   TcSmem* s = sc.s;
   const uint32_t t = threadIdx.x;
   const uint32_t lane_base = (t & ~31u) << 16;  // TMEM lane field of this warp
-  // X: hist / 16 is a multiple of 1/16 in [0, 1] (at most 16 processes in a state), exact in BF16
+  // X: the fraction of the state's processes in each local state, hist * (1 / sum hist)
+  // in FP32, rounded to BF16 (0 for an empty row)
   {
+    const float inv = feature_scale(hw);
     uint32_t q[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const uint32_t w = hw[i >> 1];
       const uint32_t sh = (i & 1) * 16;
-      q[i] = pack_bf16x2((float)((w >> sh) & 0xFFu) * (1.0f / 16.0f), (float)((w >> (sh + 8)) & 0xFFu) * (1.0f / 16.0f));
+      q[i] = pack_bf16x2((float)((w >> sh) & 0xFFu) * inv, (float)((w >> (sh + 8)) & 0xFFu) * inv);
     }
     *reinterpret_cast<uint4*>(s->x + core_offset(t, 0, 2)) = make_uint4(q[0], q[1], q[2], q[3]);
     *reinterpret_cast<uint4*>(s->x + core_offset(t, 8, 2)) = make_uint4(q[4], q[5], q[6], q[7]);

@@ -242,13 +242,14 @@ def test_mlp_oracle_gradient_matches_finite_differences():
     rng = np.random.default_rng(0)
     p = (rng.standard_normal(mlp.NPARAM) * 0.2).astype(np.float32)
     hist = rng.integers(0, 5, size=(12, 16))
+    hist[:, 0] += 1  # no empty row
     label = rng.random(12)
     _, g = mlp.loss_and_grad(p, hist, label, bf16=False)
     pd = p.astype(np.float64)
 
     def loss_at(q):
         W1, b1, W2, b2, w3, b3 = mlp.unpack(q.astype(np.float32))  # layout only
-        x = hist / 16.0
+        x = hist / hist.sum(axis=1, keepdims=True)
         a1 = x @ q[:mlp.H * mlp.IN].reshape(mlp.H, mlp.IN).T + q[mlp.H * mlp.IN:mlp.H * mlp.IN + mlp.H]
         o = mlp.H * mlp.IN + mlp.H
         W2q = q[o:o + mlp.H * mlp.H].reshape(mlp.H, mlp.H); o += mlp.H * mlp.H
@@ -298,3 +299,24 @@ def test_mlp_oracle_rounds_the_hidden_layer_input_to_bf16():
         hist = np.array([[3] + [0] * 15, [0] * 15 + [16]])
         assert (mlp.forward(p, hist) == want).all()
         assert (mlp.forward(p, hist, bf16=False) == np.float64(np.float32(pre))).all()
+
+
+def test_mlp_oracle_features_are_bf16_fractions_of_processes():
+    """Closed-form case: W1 picks input 0 into hidden unit 0 (weight 1), W2 and
+    w3 pass hidden unit 0 to the output, all biases 0, so y = x0.  x0 is the
+    fraction of processes in local state 0, rounded to bfloat16 from its
+    binary32 value: 1/3 -> 0.333984375 and 2/3 -> 0.66796875 (round up past
+    the halfway point), 1/4 and 1 exact, 0 for an empty row."""
+    from oracle import mlp
+    p = np.zeros(mlp.NPARAM, dtype=np.float32)
+    p[0] = 1.0                                            # W1[0, 0]
+    o = mlp.H * mlp.IN + mlp.H
+    p[o] = 1.0                                            # W2[0, 0]
+    p[o + mlp.H * mlp.H + mlp.H] = 1.0                    # w3[0]
+    rows = np.zeros((5, 16), dtype=np.int64)
+    rows[0, :2] = (1, 2)
+    rows[1, :2] = (2, 1)
+    rows[2, :2] = (3, 9)
+    rows[3, 0] = 16
+    y = mlp.forward(p, rows)
+    assert y.tolist() == [0.333984375, 0.66796875, 0.25, 1.0, 0.0]
