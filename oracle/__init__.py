@@ -41,7 +41,9 @@ class OracleResult(ctypes.Structure):
         "states", "explored", "transitions", "n_levels", "deadlock_count", "deadlock_sum",
         "deadlock_xor", "set_sum", "set_xor")] + [
         ("first_deadlock_level", ctypes.c_int64), ("complete", ctypes.c_uint64),
-        ("seconds", ctypes.c_double)]
+        ("seconds", ctypes.c_double), ("violation_count", ctypes.c_uint64),
+        ("violation_sum", ctypes.c_uint64), ("violation_xor", ctypes.c_uint64),
+        ("first_violation_level", ctypes.c_int64)]
 
 
 def _load():
@@ -54,7 +56,8 @@ def _load():
                     ctypes.c_uint32, u32p, u32p]
         lib.oracle_explore.argtypes = net_args + [
             ctypes.c_uint32, ctypes.c_uint64, P(OracleResult), P(ctypes.c_uint64),
-            ctypes.c_uint32, u32p, ctypes.c_uint32]
+            ctypes.c_uint32, u32p, ctypes.c_uint32,
+            ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, u32p, ctypes.c_uint32]
         lib.oracle_explore.restype = ctypes.c_int
         lib.oracle_state_digest.argtypes = [ctypes.c_uint32, u32p]
         lib.oracle_state_digest.restype = ctypes.c_uint64
@@ -98,19 +101,31 @@ class Exploration:
     complete: bool
     seconds: float
     deadlocks: np.ndarray  # (min(count, cap), n_procs) local states
+    violation_count: int = 0
+    violation_sum: int = 0
+    violation_xor: int = 0
+    first_violation_level: int = -1
+    violations: np.ndarray = None  # (min(count, cap), n_procs) local states
 
 
 def explore(net, stop_at_first_deadlock: bool = False, max_explored: int = 0,
-            levels_cap: int = 1 << 16, deadlocks_cap: int = 4096) -> Exploration:
+            levels_cap: int = 1 << 16, deadlocks_cap: int = 4096, watch=None,
+            stop_at_first_violation: bool = False, violations_cap: int = 4096) -> Exploration:
+    """Breadth-first exploration; watch = (process, local state) turns on the
+    safety check (that local state is the error state of the property automaton)."""
     lib = _load()
     f, args, keep = _net_args(net)
     res = OracleResult()
     levels = np.zeros(levels_cap, dtype=np.uint64)
     dl = np.zeros((deadlocks_cap, f["n_procs"]), dtype=np.uint32)
+    vi = np.zeros((violations_cap, f["n_procs"]), dtype=np.uint32)
+    wp, ws = (0xFFFFFFFF, 0) if watch is None else watch
+    u32p = ctypes.POINTER(ctypes.c_uint32)
     rc = lib.oracle_explore(*args, int(bool(stop_at_first_deadlock)), int(max_explored),
                             ctypes.byref(res), levels.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
-                            levels_cap, dl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
-                            deadlocks_cap)
+                            levels_cap, dl.ctypes.data_as(u32p), deadlocks_cap,
+                            int(wp), int(ws), int(bool(stop_at_first_violation)), vi.ctypes.data_as(u32p),
+                            violations_cap)
     if rc != 0:
         raise ValueError("oracle: invalid network")
     n_lv = int(res.n_levels)
@@ -118,7 +133,9 @@ def explore(net, stop_at_first_deadlock: bool = False, max_explored: int = 0,
                        [int(x) for x in levels[:min(n_lv, levels_cap)]], int(res.deadlock_count),
                        int(res.deadlock_sum), int(res.deadlock_xor), int(res.set_sum),
                        int(res.set_xor), int(res.first_deadlock_level), bool(res.complete),
-                       float(res.seconds), dl[:min(int(res.deadlock_count), deadlocks_cap)].copy())
+                       float(res.seconds), dl[:min(int(res.deadlock_count), deadlocks_cap)].copy(),
+                       int(res.violation_count), int(res.violation_sum), int(res.violation_xor),
+                       int(res.first_violation_level), vi[:min(int(res.violation_count), violations_cap)].copy())
 
 
 def state_digest(local_states) -> int:

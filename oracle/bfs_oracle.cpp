@@ -19,7 +19,11 @@
 //     (Sec. 4: the hash table keeps the open and closed sets of a BFS);
 //   * transitions are counted with multiplicity over explored states, and a
 //     state with no outgoing transition is a deadlock (Sec. 1/3, on-the-fly
-//     deadlock checking).
+//     deadlock checking);
+//   * safety checking (Sec. 3: the negation of a safety property is added to
+//     the network as one more automaton): an explored state whose watched
+//     process is in the watched local state -- the automaton's error state --
+//     is a violation.
 //
 // Digest of a state set (a definition shared by specification with the GPU
 // path, implemented here on its own): for a global state with local states
@@ -184,6 +188,9 @@ typedef struct oracle_result {
   int64_t first_deadlock_level; // -1 if none
   uint64_t complete;            // 1 if the search ran to the end (no early stop)
   double seconds;               // wall time of the search itself
+  uint64_t violation_count;     // explored states with local state watch_state in watch_proc
+  uint64_t violation_sum, violation_xor;
+  int64_t first_violation_level; // -1 if none
 } oracle_result;
 
 // Breadth-first exploration.  stop_at_first_deadlock: finish the level in
@@ -191,19 +198,24 @@ typedef struct oracle_result {
 // level during which this many states had been explored (0 = no limit);
 // used only to time a bounded sample.  levels_out[k] = size of level k;
 // deadlocks_out receives up to deadlocks_cap deadlock states (n_procs local
-// states each), in discovery order.
+// states each), in discovery order.  watch_proc < n_procs turns on the
+// safety check (violations_out as deadlocks_out); stop_at_first_violation
+// finishes the level of the first violation, then stops.
 int oracle_explore(uint32_t n_procs, uint32_t n_labels, const uint32_t* n_states,
                    const uint32_t* initial, const uint32_t* edge_off, const uint32_t* edges,
                    uint32_t n_rules, const uint32_t* rule_off, const uint32_t* rule_parts,
                    uint32_t stop_at_first_deadlock, uint64_t max_explored,
                    oracle_result* res, uint64_t* levels_out, uint32_t levels_cap,
-                   uint32_t* deadlocks_out, uint32_t deadlocks_cap) {
+                   uint32_t* deadlocks_out, uint32_t deadlocks_cap,
+                   uint32_t watch_proc, uint32_t watch_state, uint32_t stop_at_first_violation,
+                   uint32_t* violations_out, uint32_t violations_cap) {
   Net net;
   if (decode(net, n_procs, n_labels, n_states, initial, edge_off, edges, n_rules, rule_off,
              rule_parts))
     return 1;
   std::memset(res, 0, sizeof(*res));
   res->first_deadlock_level = -1;
+  res->first_violation_level = -1;
   auto t0 = std::chrono::steady_clock::now();
 
   std::unordered_set<std::string> visited;
@@ -233,6 +245,15 @@ int oracle_explore(uint32_t n_procs, uint32_t n_labels, const uint32_t* n_states
         res->deadlock_xor ^= h;
         if (res->first_deadlock_level < 0) res->first_deadlock_level = (int64_t)sizes.size() - 1;
       }
+      if (watch_proc < n_procs && get_local(net, s, watch_proc) == watch_state) {
+        uint64_t h = state_digest(net, s);
+        if (res->violation_count < violations_cap)
+          unpack(net, s, violations_out + res->violation_count * n_procs);
+        res->violation_count++;
+        res->violation_sum += h;
+        res->violation_xor ^= h;
+        if (res->first_violation_level < 0) res->first_violation_level = (int64_t)sizes.size() - 1;
+      }
       for (const std::string& t : succ) {
         if (visited.insert(t).second) {
           uint64_t h = state_digest(net, t);
@@ -243,6 +264,7 @@ int oracle_explore(uint32_t n_procs, uint32_t n_labels, const uint32_t* n_states
       }
     }
     if (stop_at_first_deadlock && res->deadlock_count > 0) stop = true;
+    if (stop_at_first_violation && res->violation_count > 0) stop = true;
     if (max_explored && res->explored >= max_explored) stop = true;
     level.swap(next);
   }

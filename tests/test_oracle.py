@@ -320,3 +320,56 @@ def test_mlp_oracle_features_are_bf16_fractions_of_processes():
     rows[3, 0] = 16
     y = mlp.forward(p, rows)
     assert y.tolist() == [0.333984375, 0.66796875, 0.25, 1.0, 0.0]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_safety_watch_closed_forms_without_rules(seed):
+    """Independent processes: the states with process p in local state s are
+    every combination of the other processes' reachable local states, so
+    there are prod_{q != p} |R_q| violations (0 if s is unreachable in p's
+    LTS).  Their digest is the digest of that product set.  The first one is
+    at p's local BFS depth of s, where the only violating state has every
+    other process still in its initial state."""
+    net = inputs.no_sync_network(seed, n_procs=4, n_states=6, deg_lo=0, deg_hi=3)
+    facts = [_local_facts(pr) for pr in net.procs]
+    for p in range(4):
+        for s in range(6):
+            d = facts[p][0]
+            r = oracle.explore(net, watch=(p, s))
+            if s not in d:
+                assert (r.violation_count, r.first_violation_level) == (0, -1)
+                continue
+            others = [sorted(facts[q][0]) for q in range(4) if q != p]
+            combos = [c[:p] + (s,) + c[p:] for c in product(*others)]
+            assert r.violation_count == len(combos)
+            hs = [oracle.state_digest(list(c)) for c in combos]
+            assert r.violation_sum == sum(hs) % (1 << 64)
+            x = 0
+            for h in hs:
+                x ^= h
+            assert r.violation_xor == x
+            assert r.first_violation_level == d[s]
+            r1 = oracle.explore(net, watch=(p, s), stop_at_first_violation=True)
+            init = [pr.initial for pr in net.procs]
+            init[p] = s
+            assert r1.violation_count == 1 and r1.violations[0].tolist() == init
+            # levels 0..depth are explored (the next one is built, not expanded)
+            assert r1.explored == sum(r.levels[:d[s] + 1])
+            assert r1.levels[:d[s] + 1] == r.levels[:d[s] + 1]
+
+
+@pytest.mark.parametrize("n_nodes", [2, 3, 4, 5, 6])
+def test_safety_watch_token_ring_closed_forms(n_nodes):
+    """Token ring (Sec. 5.2), watching node k in h1 (local state 4).  The token
+    holder is unique, so node k holds it in h1 in 3^(N-1) states (every other
+    node in i0, i1 or i2).  The shortest path there takes 1 + 4k steps: node 0
+    goes h0 -> h1, then each node j = 1..k makes two idle steps, receives the
+    token, and goes h0 -> h1.  At that depth exactly one state violates."""
+    net = inputs.token_ring(n_nodes)
+    for k in range(n_nodes):
+        r = oracle.explore(net, watch=(k, 4))
+        assert r.violation_count == 3 ** (n_nodes - 1)
+        assert r.first_violation_level == 1 + 4 * k
+        r1 = oracle.explore(net, watch=(k, 4), stop_at_first_violation=True)
+        assert r1.violation_count == 1
+        assert r1.violations[0, k] == 4
