@@ -135,6 +135,15 @@ typedef struct gx_explore_opts {
                                     (mid network: 21 % fewer bucket reads, 8 % faster) */
   float guided_scale;            /* GX_DL_GUIDED: score at which a state falls in the last
                                     bin (scores are predicted distances / max_dist); 0 = 1.0 */
+  uint32_t watch;                /* 1 = safety check (Sec. 3: the negation of a safety property
+                                    is added to the network as one more automaton): an explored
+                                    state whose process watch_proc is in local state watch_state
+                                    (the automaton's error state) is a violation.  BFS searches
+                                    only (gx_explore, GX_DL_BFS_*) */
+  uint32_t watch_proc, watch_state;
+  uint32_t stop_at_first_violation; /* 1 = stop after the level holding the first violation
+                                    (every violation of that level is reported) */
+  uint32_t violation_cap;        /* violating states kept for gx_violations; 0 = 1024 */
 } gx_explore_opts;
 
 /* Fill *opts with the defaults described above. */
@@ -162,8 +171,8 @@ gx_status gx_explore(gx_net* net, const gx_explore_opts* opts, void* workspace,
  *   mode GX_DL_BFS_ALL: full exploration, every deadlock reported;
  *   mode GX_DL_GUIDED: best-first order by the scoring network set with
  *     gx_guided_set_weights: each iteration expands the guided_batch open
- *     states of the best non-empty priority bin (last in, first out), scoring
- *     every new state as it is found.  Every state is pushed and eventually
+ *     states of the best non-empty priority bin (last in, first out), then
+ *     scores the states it inserted (on the tensor cores) into their bins.  Every state is pushed and eventually
  *     expanded, so the search is exhaustive: it stops at the first deadlock
  *     (reported with its path, gx_guided_trace) and reports absence only after
  *     the whole state space was explored.  Workspace: gx_guided_workspace_bytes.
@@ -199,6 +208,10 @@ typedef struct gx_stats_t {
   uint64_t h2d_bytes;       /* host-to-device bytes the search copied (network tables) */
   uint64_t d2h_bytes;       /* device-to-host bytes it copied (progress, deadlock states) */
   uint64_t partitioned_levels; /* levels expanded by the partitioned path */
+  uint64_t violation_count; /* explored states violating the watched property (opts.watch) */
+  uint64_t violation_sum;   /* order-free digest of the violation set, as for deadlocks */
+  uint64_t violation_xor;
+  int64_t first_violation_level; /* -1 if none */
 } gx_stats_t;
 
 gx_status gx_stats(const gx_net* net, gx_stats_t* out);
@@ -217,6 +230,11 @@ gx_status gx_level_profile(const gx_net* net, double* ms, uint64_t* probes, uint
 /* Deadlock states kept by the last search (at most opts.deadlock_cap), n_procs
  * local states each, in no particular order.  *n gets the number written. */
 gx_status gx_deadlocks(const gx_net* net, uint32_t* out, uint32_t cap, uint32_t* n);
+
+/* Violating states kept by the last search with opts.watch set (at most
+ * opts.violation_cap), n_procs local states each, in no particular order.
+ * *n gets the number written. */
+gx_status gx_violations(const gx_net* net, uint32_t* out, uint32_t cap, uint32_t* n);
 
 /* Digest of every state in the hash table after a search: count, sum and xor
  * of h(state) (same h as the deadlock digest).  workspace/stream must be the

@@ -112,12 +112,13 @@ constexpr int kPartCtas = 1024;  // CTAs of the partitioned count/scatter passes
 struct Plan {
   int W = 0, B = 0, G = 0, rounds = 0;
   uint32_t dl_cap = 0;
+  uint32_t viol_cap = 0;   // violating states kept (safety check)
   uint64_t nb = 0;         // buckets (power of two)
   uint64_t fcap = 0;       // frontier ring capacity (power of two)
   int logp = 0;            // table slices for the partitioned path (0 = path off)
   uint64_t cs = 0;         // successor buffer capacity (vectors)
   uint64_t part_min = 0;   // smallest level that may use the partitioned path
-  uint64_t off_ctl = 0, off_blob = 0, off_dl = 0, off_front = 0, off_table = 0;
+  uint64_t off_ctl = 0, off_blob = 0, off_dl = 0, off_viol = 0, off_front = 0, off_table = 0;
   uint64_t off_hist = 0, off_off = 0, off_ptot = 0, off_tot = 0, off_succ = 0;
   uint64_t total = 0;
   const KernelSet* ks = nullptr;
@@ -150,6 +151,12 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
   const uint64_t slots = P.nb * (uint64_t)S;
   P.fcap = pow2_ceil(o->frontier_states ? o->frontier_states : std::max<uint64_t>(4096, slots / 4));
   P.dl_cap = o->deadlock_cap ? o->deadlock_cap : 1024;
+  if (o->watch) {
+    if (o->watch_proc >= net.n_procs) return fail(GX_ERR_INVALID, "watch_proc is not a process of the network");
+    if (o->watch_state >= net.n_states[o->watch_proc])
+      return fail(GX_ERR_INVALID, "watch_state is not a local state of watch_proc");
+    P.viol_cap = o->violation_cap ? o->violation_cap : 1024;
+  }
   // partitioned path: slices of about 32 MiB, at most 4096 of them
   const uint64_t tbytes = 4ull * P.B * P.nb;
   if (o->slice_log2) {
@@ -172,6 +179,8 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
   off = align_up(off + 4ull * net.blob.size());
   P.off_dl = off;
   off = align_up(off + 4ull * P.W * P.dl_cap);
+  P.off_viol = off;
+  off = align_up(off + 4ull * P.W * P.viol_cap);
   P.off_front = off;
   off = align_up(off + 4ull * P.W * P.fcap);
   P.off_table = off;
@@ -311,6 +320,17 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   ea.ctl = ctl;
   ea.dl_buf = dl;
   ea.dl_cap = P.dl_cap;
+  uint32_t* viol = reinterpret_cast<uint32_t*>(base + P.off_viol);
+  if (o->watch) {
+    const uint32_t wp = o->watch_proc;
+    ea.watch = 1;
+    ea.watch_word = net.field_word[wp];
+    ea.watch_shift = net.field_shift[wp];
+    ea.watch_mask = (1u << net.field_bits[wp]) - 1u;
+    ea.watch_value = o->watch_state;
+    ea.viol_buf = viol;
+    ea.viol_cap = P.viol_cap;
+  }
   size_t smem = 8ull * kMaxRounds;
   const size_t blob_bytes = 4ull * net.blob.size();
   ea.stage = (smem + blob_bytes <= std::min<size_t>(dev.smem_optin, 96 * 1024)) ? 1 : 0;
@@ -334,7 +354,8 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
 
   std::vector<uint64_t> levels{1};
   uint64_t cur_begin = 0, cur_end = 1, explored = 0;
-  int64_t first_dl = -1;
+  int64_t first_dl = -1, first_viol = -1;
+  const bool stop_viol = o->watch && o->stop_at_first_violation;
   double expand_ms = 0;
   uint64_t launches = 0, levels_done = 0;
   uint32_t err = 0;
@@ -420,6 +441,7 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
     prev_trans = hc->transitions;
     explored += cur_end - cur_begin;
     if (first_dl < 0 && hc->dl_count > 0) first_dl = (int64_t)levels.size() - 1;
+    if (first_viol < 0 && hc->viol_count > 0) first_viol = (int64_t)levels.size() - 1;
     err = hc->error;
     const uint64_t next_end = hc->next_end;
     if (next_end > cur_end) levels.push_back(next_end - cur_end);
@@ -431,6 +453,7 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
     cur_begin = cur_end;
     cur_end = next_end;
     if (stop_first && hc->dl_count > 0) break;
+    if (stop_viol && hc->viol_count > 0) break;
     if (o->max_levels && levels_done >= o->max_levels) break;
   }
   GX_CUDA(cudaEventRecord(ev1, st));
@@ -452,6 +475,20 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
     unpack_host(net, w4, h->deadlocks.data() + i * net.n_procs);
   }
 
+  // violating states (safety check)
+  const uint64_t nvi = std::min<uint64_t>(hc->viol_count, P.viol_cap);
+  std::vector<uint32_t> viw(nvi * P.W);
+  if (nvi) {
+    GX_CUDA(cudaMemcpyAsync(viw.data(), viol, 4 * viw.size(), cudaMemcpyDeviceToHost, st));
+    GX_CUDA(cudaStreamSynchronize(st));
+  }
+  h->violations.assign(nvi * net.n_procs, 0);
+  for (uint64_t i = 0; i < nvi; ++i) {
+    uint32_t w4[4] = {0, 0, 0, 0};
+    for (int w = 0; w < P.W; ++w) w4[w] = viw[i * P.W + w];
+    unpack_host(net, w4, h->violations.data() + i * net.n_procs);
+  }
+
   gx_stats_t& S = h->stats;
   std::memset(&S, 0, sizeof(S));
   S.states = hc->next_end;
@@ -462,6 +499,10 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   S.deadlock_sum = hc->dl_sum;
   S.deadlock_xor = hc->dl_xor;
   S.first_deadlock_level = first_dl;
+  S.violation_count = hc->viol_count;
+  S.violation_sum = hc->viol_sum;
+  S.violation_xor = hc->viol_xor;
+  S.first_violation_level = first_viol;
   S.table_slots = P.nb * (uint64_t)(P.B / P.W);
   S.vector_words = net.vector_words;
   S.slot_words = (uint32_t)P.W;
@@ -476,7 +517,7 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   S.probes = hc->probes;
   S.partitioned_levels = part_levels;
   S.h2d_bytes = 4ull * net.blob.size();
-  S.d2h_bytes = sizeof(Ctl) * levels_done + 4ull * dlw.size() + d2h_tot;
+  S.d2h_bytes = sizeof(Ctl) * levels_done + 4ull * (dlw.size() + viw.size()) + d2h_tot;
   h->levels = levels;
   h->level_ms = lv_ms;
   h->level_probes = lv_probes;
@@ -526,6 +567,7 @@ gx_status gx_find_deadlocks(gx_net* h, const gx_explore_opts* opts, uint32_t mod
   if (mode == GX_DL_BFS_FIRST || mode == GX_DL_BFS_ALL) {
     s = gx::run_search(h, opts, mode == GX_DL_BFS_FIRST, ws, ws_bytes, static_cast<cudaStream_t>(stream));
   } else if (mode == GX_DL_GUIDED) {
+    if (opts && opts->watch) return gx::fail(GX_ERR_INVALID, "the safety check (watch) runs with BFS searches only");
     s = gx::run_guided(h, opts, ws, ws_bytes, static_cast<cudaStream_t>(stream));
   } else {
     return gx::fail(GX_ERR_INVALID, "unknown deadlock-search mode");
@@ -568,6 +610,19 @@ gx_status gx_level_profile(const gx_net* h, double* ms, uint64_t* probes, uint64
     if (probes) probes[i] = h->level_probes[i];
     if (transitions) transitions[i] = h->level_transitions[i];
   }
+  if (n) *n = (uint32_t)k;
+  return GX_OK;
+}
+
+gx_status gx_violations(const gx_net* h, uint32_t* out, uint32_t cap, uint32_t* n) {
+  gx::clear_error();
+  if (!h) return gx::fail(GX_ERR_INVALID, "net is NULL");
+  if (!h->have_result) return gx::fail(GX_ERR_STATE, "no search has run on this network");
+  if (cap && !out) return gx::fail(GX_ERR_INVALID, "out is NULL");
+  const uint32_t np = h->net.n_procs;
+  const uint64_t have = h->violations.size() / np;
+  const uint64_t k = std::min<uint64_t>(have, cap);
+  if (k) std::memcpy(out, h->violations.data(), 4ull * np * k);
   if (n) *n = (uint32_t)k;
   return GX_OK;
 }

@@ -632,6 +632,7 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
   // the path of the deadlock: follow parent log indices back to the initial state
   h->guided_trace.clear();
   h->deadlocks.clear();
+  h->violations.clear();
   const int E = P.W + 1;
   if (hc.found != ~0ull) {
     std::vector<std::vector<uint32_t>> path;

@@ -63,6 +63,7 @@ struct gx_net {
   std::vector<double> level_ms;
   std::vector<uint64_t> level_probes, level_transitions;
   std::vector<uint32_t> deadlocks;  // unpacked, n_procs per state
+  std::vector<uint32_t> violations; // unpacked, n_procs per state (safety check)
   // workspace regions of the last search (for gx_set_digest, gx_training_set)
   uint64_t ws_off_ctl = 0, ws_off_blob = 0, ws_off_table = 0, ws_total = 0;
   // guided search: scoring weights (device, caller-owned) and the last deadlock's path

@@ -144,6 +144,25 @@ __device__ __forceinline__ void store_vec(uint32_t* p, const uint32_t (&v)[W]) {
   }
 }
 
+// Safety check (Sec. 3: the negated property is one more automaton of the
+// network): v violates when its watched field holds the automaton's error
+// state.  A violation is counted, folded into the violation digest and kept
+// while there is room.
+template <int W>
+__device__ __forceinline__ void check_watch(const gx::ExpandArgs& a, const uint32_t* t, const NetBlobLayout& L,
+                                            const uint32_t (&v)[W]) {
+  uint32_t w = v[0];
+#pragma unroll
+  for (int i = 1; i < W; ++i)
+    if (a.watch_word == (uint32_t)i) w = v[i];
+  if (((w >> a.watch_shift) & a.watch_mask) != a.watch_value) return;
+  const uint64_t h = state_digest<W>(t, L, v);
+  const unsigned long long vi = atomicAdd(&a.ctl->viol_count, 1ull);
+  atomicAdd(&a.ctl->viol_sum, (unsigned long long)h);
+  atomicXor(&a.ctl->viol_xor, (unsigned long long)h);
+  if (vi < a.viol_cap) store_vec<W>(a.viol_buf + vi * W, v);
+}
+
 __device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULLMASK, x, o);
@@ -385,6 +404,7 @@ __global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(
       atomicXor(&a.ctl->dl_xor, (unsigned long long)h);
       if (di < a.dl_cap) store_vec<W>(a.dl_buf + di * W, v);
     }
+    if (a.watch && valid) check_watch<W>(a, t, L, v);
     SuccIter it;
     it.init();
     constexpr int K = PerLane<G>::K;
@@ -556,6 +576,7 @@ __global__ void __launch_bounds__(gx::kBlock) part_scatter_kernel(const gx::Expa
       atomicXor(&a.ctl->dl_xor, (unsigned long long)h);
       if (di < a.dl_cap) store_vec<W>(a.dl_buf + di * W, v);
     }
+    if (a.watch) check_watch<W>(a, t, L, v);
     SuccIter it;
     it.init();
     for (uint32_t k = 0; k < cnt; ++k) {

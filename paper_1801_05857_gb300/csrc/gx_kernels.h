@@ -24,6 +24,7 @@ struct Ctl {
   unsigned int error;              // ERR_* bits
   unsigned int pad;
   unsigned long long digest[3];    // gx_set_digest: count, sum, xor
+  unsigned long long viol_count, viol_sum, viol_xor;  // safety check
 };
 static_assert(sizeof(Ctl) <= 256, "control block");
 
@@ -48,6 +49,11 @@ struct ExpandArgs {
   uint32_t* dl_buf;          // deadlock vectors, W words each
   uint32_t dl_cap;
   int cache_log2;            // per-warp cache of recently seen vectors: 2^cache_log2 entries (0 = off)
+  // safety check: a state whose field (word, shift, mask) equals watch_value violates
+  int watch;
+  uint32_t watch_word, watch_shift, watch_mask, watch_value;
+  uint32_t* viol_buf;        // violating vectors, W words each
+  uint32_t viol_cap;
 };
 
 // Partitioned expansion of one level (or one batch of it): successors are

@@ -54,7 +54,8 @@ class gx_explore_opts(ctypes.Structure):
                 ("ctas_per_sm", u32), ("guided_batch", u32), ("table_bytes", u64),
                 ("frontier_states", u64), ("successor_buffer", u64), ("slice_log2", u32),
                 ("partition_min_states", u32), ("guided_bins", u32), ("warp_cache_log2", u32),
-                ("guided_scale", ctypes.c_float)]
+                ("guided_scale", ctypes.c_float), ("watch", u32), ("watch_proc", u32),
+                ("watch_state", u32), ("stop_at_first_violation", u32), ("violation_cap", u32)]
 
 
 MLP_IN, MLP_HIDDEN = 16, 128
@@ -73,7 +74,9 @@ class gx_stats_t(ctypes.Structure):
                 ("group_lanes", u32), ("hash_rounds", u32), ("complete", u32), ("status", u32),
                 ("reserved", u32), ("fill", ctypes.c_double), ("gpu_ms", ctypes.c_double),
                 ("expand_ms", ctypes.c_double), ("expand_launches", u64), ("probes", u64),
-                ("h2d_bytes", u64), ("d2h_bytes", u64), ("partitioned_levels", u64)]
+                ("h2d_bytes", u64), ("d2h_bytes", u64), ("partitioned_levels", u64),
+                ("violation_count", u64), ("violation_sum", u64), ("violation_xor", u64),
+                ("first_violation_level", ctypes.c_int64)]
 
 
 class gx_batch_opts(ctypes.Structure):
@@ -115,6 +118,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "gx_stats": ([vp, P(gx_stats_t)], ctypes.c_int),
         "gx_levels": ([vp, P(u64), u32, P(u32)], ctypes.c_int),
         "gx_deadlocks": ([vp, P(u32), u32, P(u32)], ctypes.c_int),
+        "gx_violations": ([vp, P(u32), u32, P(u32)], ctypes.c_int),
         "gx_level_profile": ([vp, P(ctypes.c_double), P(u64), P(u64), u32, P(u32)], ctypes.c_int),
         "gx_set_digest": ([vp, vp, u64, vp, P(u64), P(u64), P(u64)], ctypes.c_int),
         "gx_find_or_put": ([vp, u64, u32, u32, u32, u32, vp, u64, vp, vp, vp], ctypes.c_int),
@@ -306,6 +310,14 @@ def deadlocks(net: Net, cap: int = 1 << 20) -> np.ndarray:
     out = np.zeros((cap, net.n_procs), dtype=np.uint32)
     n = u32()
     _check(lib().gx_deadlocks(net.handle, out.ctypes.data_as(P(u32)), cap, ctypes.byref(n)))
+    return out[:int(n.value)].copy()
+
+
+def violations(net: Net, cap: int = 1 << 20) -> np.ndarray:
+    """Violating states of the last search with opts.watch (n_procs local states each)."""
+    out = np.zeros((cap, net.n_procs), dtype=np.uint32)
+    n = u32()
+    _check(lib().gx_violations(net.handle, out.ctypes.data_as(P(u32)), cap, ctypes.byref(n)))
     return out[:int(n.value)].copy()
 
 
