@@ -89,6 +89,39 @@ gx_status gx_load_network(const gx_net_desc* desc, gx_net** out);
 /* Release a network and everything the library holds for it.  NULL is a no-op. */
 void gx_free(gx_net* net);
 
+/* A network in the paper's input format (Sec. 3, Fig. 1): an EXP.OPEN
+ * composition
+ *     par using v_1, ..., v_m in "f_1" || ... || "f_n" end par
+ * ("using v_1, ..., v_m" may be left out), where each synchronisation vector
+ * v_j is  l_1 * ... * l_n -> r : one label per process, or '_' for a process
+ * that does not take part, and the result label r.  Each "f_i" names an LTS
+ * given in Aldebaran format:
+ *     des (initial, n_transitions, n_states)
+ *     (src, "label", dst)        one line per transition
+ * Labels are global strings (quotes optional where a label has no comma,
+ * quote or parenthesis); a (process, label) pair occurring in some vector
+ * moves only through vectors, every other transition interleaves.
+ * Comments (* ... *) may appear in the composition.
+ * exp_text: the composition; file_names / file_texts: n_files names (as
+ * written between the quotes) and contents, host memory, copied.  Several
+ * processes may name the same file.  On success *out is a network as from
+ * gx_load_network, with label names for gx_label_name.  GX_ERR_INVALID with a
+ * message naming the file and line on a syntax error, a vector whose length
+ * differs from the number of processes, a file not given, a state out of
+ * range or a transition count that does not match the des header. */
+gx_status gx_load_exp(const char* exp_text, uint32_t n_files, const char* const* file_names,
+                      const char* const* file_texts, gx_net** out);
+
+/* Name of label `label` of a network from gx_load_exp (the decimal index for
+ * networks from gx_load_network), NUL-terminated into buf (cap bytes,
+ * truncated); *len gets the full length. */
+gx_status gx_label_name(const gx_net* net, uint32_t label, char* buf, uint32_t cap, uint32_t* len);
+
+/* Sizes of a loaded network: processes, labels, synchronisation rules and
+ * transitions over all process LTSs.  Any output may be NULL. */
+gx_status gx_network_counts(const gx_net* net, uint32_t* n_procs, uint32_t* n_labels, uint32_t* n_rules,
+                            uint64_t* n_edges);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* gx_last_error(void);
 

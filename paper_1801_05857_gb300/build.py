@@ -25,7 +25,7 @@ LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libgx.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gx_net.cpp", "gx_explore.cu", "gx_table.cu", "gx_noalloc.cu", "gx_batch.cu",
+SOURCES = ["gx_net.cpp", "gx_text.cpp", "gx_explore.cu", "gx_table.cu", "gx_noalloc.cu", "gx_batch.cu",
            "gx_mlp.cu", "gx_guided.cu",
            "gx_kernels_w1.cu", "gx_kernels_w2.cu", "gx_kernels_w4.cu"]
 

@@ -46,6 +46,7 @@ struct Net {
   // edges from one state, plus per rule the product over its participants of
   // the most matching edges from one state (capped at 2^40)
   uint64_t max_succ = 0;
+  uint64_t n_edges = 0;  // transitions over all process LTSs
   std::vector<uint32_t> blob;
   NetBlobLayout lay{};
   uint32_t init_vec[kMaxWords] = {0, 0, 0, 0};
@@ -69,6 +70,8 @@ struct gx_net {
   // guided search: scoring weights (device, caller-owned) and the last deadlock's path
   const float* guided_params = nullptr;
   std::vector<uint32_t> guided_trace;
+  // label names of a network read from text (gx_load_exp); empty otherwise
+  std::vector<std::string> label_names;
 };
 
 namespace gx {

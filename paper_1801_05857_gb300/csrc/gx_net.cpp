@@ -82,6 +82,7 @@ static gx_status encode(const gx_net_desc* d, Net& net) {
     }
     net.n_states[p] = P.n_states;
     net.initial[p] = P.initial;
+    net.n_edges += P.n_edges;
     uint32_t b = bits_for(P.n_states);
     if (shift + b > kPayloadBits) {
       ++word;

@@ -108,6 +108,9 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
     sig = {
         "gx_load_network": ([P(gx_net_desc), P(vp)], ctypes.c_int),
         "gx_free": ([vp], None),
+        "gx_load_exp": ([ctypes.c_char_p, u32, P(ctypes.c_char_p), P(ctypes.c_char_p), P(vp)], ctypes.c_int),
+        "gx_label_name": ([vp, u32, ctypes.c_char_p, u32, P(u32)], ctypes.c_int),
+        "gx_network_counts": ([vp, P(u32), P(u32), P(u32), P(u64)], ctypes.c_int),
         "gx_last_error": ([], ctypes.c_char_p),
         "gx_layout": ([vp, P(u32), P(u32), P(u32), P(u32)], ctypes.c_int),
         "gx_default_opts": ([P(gx_explore_opts)], ctypes.c_int),
@@ -225,6 +228,51 @@ def load_network(net) -> Net:
     h = ctypes.c_void_p()
     _check(lib().gx_load_network(ctypes.byref(desc), ctypes.byref(h)))
     return Net(h.value, n)
+
+
+def load_exp(exp_text: str, files: dict) -> Net:
+    """gx_load_exp: an EXP.OPEN composition and the .aut texts it names
+    (files: name as written in the composition -> contents)."""
+    names = list(files)
+    n = len(names)
+    cn = (ctypes.c_char_p * max(n, 1))(*[x.encode() for x in names])
+    ct = (ctypes.c_char_p * max(n, 1))(*[files[x].encode() for x in names])
+    h = ctypes.c_void_p()
+    _check(lib().gx_load_exp(exp_text.encode(), n, cn, ct, ctypes.byref(h)))
+    np_ = u32()
+    _check(lib().gx_network_counts(h.value, ctypes.byref(np_), None, None, None))
+    return Net(h.value, int(np_.value))
+
+
+def load_exp_file(path: str) -> Net:
+    """A composition file and the .aut files it names, read relative to its directory
+    (every quoted name in the composition that is an existing file is passed on)."""
+    import os
+    import re
+    with open(path) as f:
+        text = f.read()
+    base = os.path.dirname(os.path.abspath(path))
+    files = {}
+    for name in re.findall(r'"([^"\n]+)"', text):
+        full = os.path.join(base, name)
+        if name not in files and os.path.isfile(full):
+            with open(full) as g:
+                files[name] = g.read()
+    return load_exp(text, files)
+
+
+def label_name(net: Net, label: int) -> str:
+    n = u32()
+    _check(lib().gx_label_name(net.handle, label, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(int(n.value) + 1)
+    _check(lib().gx_label_name(net.handle, label, buf, len(buf), ctypes.byref(n)))
+    return buf.value.decode()
+
+
+def network_counts(net: Net) -> dict:
+    a, b, c, d = u32(), u32(), u32(), u64()
+    _check(lib().gx_network_counts(net.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return dict(n_procs=int(a.value), n_labels=int(b.value), n_rules=int(c.value), n_edges=int(d.value))
 
 
 def layout(net: Net) -> dict:
