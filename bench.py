@@ -55,9 +55,11 @@ def parse():
     ap.add_argument("--no-table", action="store_true", help="skip the Sec. 5.1 find-or-put part")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided deadlock-search part")
-    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep", "scaled"],
+    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep", "scaled", "scaling-table"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
-                         "exploration for every (bucket, group) size; one JSON line per point")
+                         "exploration for every (bucket, group) size; scaled: one large token ring; "
+                         "scaling-table: ring and producer/consumer families by size (Table 1); "
+                         "one JSON line per point")
     return ap.parse_args()
 
 
@@ -642,6 +644,39 @@ def scaled_experiment(torch, gx, inputs, args):
     assert s["states"] == want_states and s["transitions"] == want_trans, "closed form mismatch"
 
 
+def scaling_table(torch, gx, inputs, args):
+    """Model size against throughput, as in Table 1: the token ring for N = 2..16
+    (2N 3^(N-1) states, 4 N^2 3^(N-2) transitions) and Fig. 1's producer with k
+    consumers for k = 1..30 (2^(k+1) states, 2^k + k 2^(k-1) + k 2^(k+1)
+    transitions).  Each network is explored twice in a table of at most 50 %
+    fill (the second run is reported); counts are checked against the closed forms."""
+    rows = [("token_ring", n, inputs.token_ring(n), 2 * n * 3 ** (n - 1), 4 * n * n * 3 ** (n - 2))
+            for n in range(2, 17)]
+    rows += [("producer_consumers", k, inputs.producer_consumers(k), 2 ** (k + 1),
+              2 ** k + k * 2 ** (k - 1) + k * 2 ** (k + 1)) for k in range(1, 31)]
+    for family, size, net, want_s, want_t in rows:
+        h = gx.load_network(net)
+        W = gx.layout(h)["vector_words"]
+        table = 1 << 20
+        while table < 2 * want_s * 4 * W:
+            table *= 2
+        o = gx.default_opts(table_bytes=table, hash_rounds=args.rounds)
+        ws = gx.alloc_workspace(h, o)
+        for _ in range(2):
+            gx.explore(h, o, ws)
+        s = gx.stats(h)
+        rec = {"experiment": "scaling-table", "family": family, "size": size, "processes": len(net.procs),
+               "vector_words": s["vector_words"], "states": s["states"], "transitions": s["transitions"],
+               "levels": s["n_levels"], "closed_form_ok": s["states"] == want_s and s["transitions"] == want_t,
+               "table_gib": round(table / 2 ** 30, 3), "fill": round(s["fill"], 4), "gpu_ms": round(s["gpu_ms"], 3),
+               "states_per_s": round(s["states"] / (s["gpu_ms"] * 1e-3), 1),
+               "transitions_per_s": round(s["transitions"] / (s["gpu_ms"] * 1e-3), 1)}
+        print(json.dumps(rec), flush=True)
+        del ws
+        torch.cuda.empty_cache()
+        assert rec["closed_form_ok"], "closed form mismatch"
+
+
 def run_experiment(args):
     """One JSON line per point; not the bench contract's line."""
     import torch
@@ -660,6 +695,8 @@ def run_experiment(args):
                     print(json.dumps({"experiment": "sec5.1 find-or-put", **pt}), flush=True)
                     group *= 2
             del keys
+    elif args.experiment == "scaling-table":
+        scaling_table(torch, gx, inputs, args)
     elif args.experiment == "scaled":
         scaled_experiment(torch, gx, inputs, args)
     elif args.experiment == "bucket-sweep":

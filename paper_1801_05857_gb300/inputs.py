@@ -119,18 +119,22 @@ class Network:
 # Hand-written networks
 # --------------------------------------------------------------------------------------------
 
-def producer_consumers() -> Network:
-    """The producer / two consumers network of Fig. 1.
+def producer_consumers(n_consumers: int = 2) -> Network:
+    """The producer / consumers network of Fig. 1 (two consumers there).
 
     Labels: 0 gen_work, 1 send, 2 rec, 3 work, 4 tau, 5 trans.
     Producer: p0 -gen_work-> p1, p1 -send-> p0.
     Consumer: c0 -rec-> c1, c1 -work-> c1, c1 -tau-> c0.
-    Rules: send * rec * _ -> trans and send * _ * rec -> trans.
+    Rules: one per consumer i, send (producer) * rec (consumer i) -> trans.
+    With k consumers every combination of local states is reachable:
+    2^(k+1) states and 2^k + k 2^(k-1) + k 2^(k+1) transitions (8 and 24 for
+    k = 2, the counts the paper gives for Fig. 1).
     """
     producer = LTS(2, 0, [(0, 0, 1), (1, 1, 0)])
     consumer = lambda: LTS(2, 0, [(0, 2, 1), (1, 3, 1), (1, 4, 0)])
-    rules = [Rule([(0, 1), (1, 2)], 5), Rule([(0, 1), (2, 2)], 5)]
-    return Network(6, [producer, consumer(), consumer()], rules, name="fig1_producer_consumers")
+    rules = [Rule([(0, 1), (i, 2)], 5) for i in range(1, n_consumers + 1)]
+    name = "fig1_producer_consumers" if n_consumers == 2 else f"producer_consumers_{n_consumers}"
+    return Network(6, [producer] + [consumer() for _ in range(n_consumers)], rules, name=name)
 
 
 def token_ring(n_nodes: int) -> Network:

@@ -256,3 +256,17 @@ def test_mid_config_with_warp_cache(cuda):
                            warp_cache_log2=9)
     assert (s["states"], s["transitions"], lv) == (g["states"], g["transitions"], g["levels"])
     assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])
+
+
+@pytest.mark.parametrize("k", [1, 2, 7, 16, 22])
+def test_producer_consumers_family(cuda, k):
+    """Fig. 1 with k consumers: 2^(k+1) states and 2^k + k 2^(k-1) + k 2^(k+1)
+    transitions (closed form; pinned against the oracle up to k = 10)."""
+    net = inputs.producer_consumers(k)
+    if k <= 10:
+        s = assert_parity(net, table_bytes=1 << 24)
+    else:
+        _, s, _, _ = run_gpu(net, table_bytes=1 << 27)
+    assert s["states"] == 2 ** (k + 1)
+    assert s["transitions"] == 2 ** k + k * 2 ** (k - 1) + k * 2 ** (k + 1)
+    assert s["deadlock_count"] == 0 and s["complete"] == 1

@@ -373,3 +373,19 @@ def test_safety_watch_token_ring_closed_forms(n_nodes):
         r1 = oracle.explore(net, watch=(k, 4), stop_at_first_violation=True)
         assert r1.violation_count == 1
         assert r1.violations[0, k] == 4
+
+
+@pytest.mark.parametrize("k", range(1, 11))
+def test_producer_consumers_family_closed_forms(k):
+    """Fig. 1 with k consumers.  Every combination of local states is
+    reachable (2^(k+1) states).  Counting enabled transitions per state:
+    gen_work in the 2^k states with the producer in p0; send/rec with consumer
+    i in the 2^(k-1) states with the producer in p1 and consumer i in c0, for
+    each i; work and tau of consumer i in the 2^k states with consumer i in
+    c1.  No state is a deadlock."""
+    r = oracle.explore(inputs.producer_consumers(k))
+    assert r.states == 2 ** (k + 1)
+    assert r.transitions == 2 ** k + k * 2 ** (k - 1) + k * 2 ** (k + 1)
+    assert r.deadlock_count == 0
+    if k == 2:
+        assert (r.states, r.transitions) == (8, 24)
