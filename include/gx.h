@@ -177,6 +177,13 @@ typedef struct gx_explore_opts {
   uint32_t stop_at_first_violation; /* 1 = stop after the level holding the first violation
                                     (every violation of that level is reported) */
   uint32_t violation_cap;        /* violating states kept for gx_violations; 0 = 1024 */
+  uint32_t host_loop;            /* 1 = drive the level loop from the host (one control-block
+                                    read per level, per-level CUDA-event times).  0 (default):
+                                    when the partitioned path is off, the levels run on the
+                                    device as one CUDA graph with a conditional WHILE node
+                                    (expand, then a one-thread advance step that records the
+                                    level and decides whether to go on); after 4096 levels the
+                                    host loop takes over */
 } gx_explore_opts;
 
 /* Fill *opts with the defaults described above. */
@@ -245,6 +252,9 @@ typedef struct gx_stats_t {
   uint64_t violation_sum;   /* order-free digest of the violation set, as for deadlocks */
   uint64_t violation_xor;
   int64_t first_violation_level; /* -1 if none */
+  uint64_t kernel_launches; /* kernels the search launched (initialisation, expansion,
+                               level-advance steps) */
+  uint64_t device_levels;   /* levels expanded by the device-driven loop */
 } gx_stats_t;
 
 gx_status gx_stats(const gx_net* net, gx_stats_t* out);

@@ -2,9 +2,13 @@
 //
 // One search (Sec. 3): clear the table, insert the initial vector (level 0),
 // then per level launch one persistent expansion kernel over the open
-// vectors of that level; the host only reads a 64-byte control block between
-// levels to learn the next level's size and whether an error or a deadlock
-// occurred ("only the general progress is checked on the host side", Sec. 3).
+// vectors of that level.  By default the levels run on the device: one CUDA
+// graph whose conditional WHILE node repeats {expand, advance}, where the
+// one-thread advance step records the level, moves the level range on and
+// decides whether to go on, so the host waits once per search.  With
+// host_loop (and on the partitioned path) the host reads the control block
+// between levels instead ("only the general progress is checked on the host
+// side", Sec. 3).
 //
 // Workspace (one device buffer, 256-byte aligned regions):
 //   control block | network blob | deadlock buffer |
@@ -40,7 +44,92 @@ void hash_multipliers(uint64_t* out, int n) {
 
 }  // namespace gx
 
+namespace gx {
+
+// The device-driven level loop (see run_search).
+struct LoopArgs {
+  Ctl* ctl;
+  unsigned long long* lv_size;    // [cap] level sizes (level 0 = 1)
+  unsigned long long* lv_tns;     // [cap] per expanded level: device time in ns (%globaltimer)
+  unsigned long long* lv_probes;  // [cap] cumulative bucket reads after the level
+  unsigned long long* lv_trans;   // [cap] cumulative transitions after the level
+  uint32_t cap;
+  int stop_dl, stop_viol;
+  uint64_t max_levels;            // 0 = no limit
+  cudaGraphConditionalHandle cond;
+};
+
+constexpr uint32_t kLoopLevels = 4096;  // levels the device loop records before the host takes over
+
+}  // namespace gx
+
 namespace gxd {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Level 0 = {initial state}; start the loop unless the insertion failed.
+__global__ void loop_start_kernel(const gx::LoopArgs L) {
+  gx::Ctl& c = *L.ctl;
+  c.cur_begin = 0;
+  c.cur_end = 1;
+  c.n_levels = 1;
+  c.levels_done = 0;
+  c.explored = 0;
+  c.first_dl = -1;
+  c.first_viol = -1;
+  c.complete = 0;
+  c.yielded = 0;
+  c.claim = 0;
+  L.lv_size[0] = 1;
+  c.t_prev = global_ns();
+  cudaGraphSetConditional(L.cond, c.error ? 0u : 1u);
+}
+
+// After the expansion of level [cur_begin, cur_end): the host loop's
+// bookkeeping, done on the device.
+__global__ void level_advance_kernel(const gx::LoopArgs L) {
+  gx::Ctl& c = *L.ctl;
+  const unsigned long long k = c.levels_done;
+  const unsigned long long t = global_ns();
+  if (k < L.cap) {
+    L.lv_tns[k] = t - c.t_prev;
+    L.lv_probes[k] = c.probes;
+    L.lv_trans[k] = c.transitions;
+  }
+  c.t_prev = t;
+  c.levels_done = k + 1;
+  c.explored += c.cur_end - c.cur_begin;
+  if (c.first_dl < 0 && c.dl_count > 0) c.first_dl = (long long)c.n_levels - 1;
+  if (c.first_viol < 0 && c.viol_count > 0) c.first_viol = (long long)c.n_levels - 1;
+  const unsigned long long next_end = c.next_end;
+  if (next_end > c.cur_end) {
+    if (c.n_levels < L.cap) L.lv_size[c.n_levels] = next_end - c.cur_end;
+    c.n_levels += 1;
+  }
+  bool more = true;
+  if (c.error) {
+    more = false;
+  } else if (next_end == c.cur_end) {
+    c.complete = 1;
+    more = false;
+  } else {
+    c.cur_begin = c.cur_end;
+    c.cur_end = next_end;
+    c.claim = 0;
+    if ((L.stop_dl && c.dl_count > 0) || (L.stop_viol && c.viol_count > 0) ||
+        (L.max_levels && c.levels_done >= L.max_levels)) {
+      more = false;
+    } else if (c.n_levels >= L.cap) {  // arrays full: the host loop continues from here
+      c.yielded = 1;
+      more = false;
+    }
+  }
+  cudaGraphSetConditional(L.cond, more ? 1u : 0u);
+}
 
 template <int W>
 __global__ void __launch_bounds__(gx::kBlock) digest_kernel(const gx::DigestArgs a) {
@@ -118,7 +207,7 @@ struct Plan {
   int logp = 0;            // table slices for the partitioned path (0 = path off)
   uint64_t cs = 0;         // successor buffer capacity (vectors)
   uint64_t part_min = 0;   // smallest level that may use the partitioned path
-  uint64_t off_ctl = 0, off_blob = 0, off_dl = 0, off_viol = 0, off_front = 0, off_table = 0;
+  uint64_t off_ctl = 0, off_blob = 0, off_dl = 0, off_viol = 0, off_loop = 0, off_front = 0, off_table = 0;
   uint64_t off_hist = 0, off_off = 0, off_ptot = 0, off_tot = 0, off_succ = 0;
   uint64_t total = 0;
   const KernelSet* ks = nullptr;
@@ -181,6 +270,8 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
   off = align_up(off + 4ull * P.W * P.dl_cap);
   P.off_viol = off;
   off = align_up(off + 4ull * P.W * P.viol_cap);
+  P.off_loop = off;
+  off = align_up(off + 4ull * 8ull * kLoopLevels);
   P.off_front = off;
   off = align_up(off + 4ull * P.W * P.fcap);
   P.off_table = off;
@@ -232,6 +323,79 @@ gx_status host_ctl(Ctl*& out, uint32_t*& tot) {
   if (!g_hctl.tot) GX_CUDA(cudaMallocHost(reinterpret_cast<void**>(&g_hctl.tot), 4ull * kPartCtas));
   out = g_hctl.p;
   tot = g_hctl.tot;
+  return GX_OK;
+}
+
+void release_loop(gx_net* h) {
+  if (h->loop_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->loop_exec));
+  if (h->loop_graph) cudaGraphDestroy(static_cast<cudaGraph_t>(h->loop_graph));
+  h->loop_exec = nullptr;
+  h->loop_graph = nullptr;
+  h->loop_key.clear();
+}
+
+// The device-driven search as one graph: clear the control block and the
+// table, insert the initial vector, start, then WHILE(cond) {expand; advance}.
+gx_status build_loop_graph(gx_net* h, const Plan& P, Ctl* ctl, uint32_t* table, const InitArgs& ia,
+                           const ExpandArgs& eg, LoopArgs la, size_t smem, uint64_t grid) {
+  release_loop(h);
+  h->release = &release_loop;
+  cudaGraph_t g;
+  GX_CUDA(cudaGraphCreate(&g, 0));
+  h->loop_graph = g;
+  cudaGraphConditionalHandle cond;
+  GX_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  la.cond = cond;
+  std::vector<cudaGraphNode_t> clears;
+  auto add_memset = [&](void* dst, uint64_t words) -> cudaError_t {
+    cudaMemsetParams mp{};
+    mp.dst = dst;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = words;
+    mp.height = 1;
+    cudaGraphNode_t nd;
+    cudaError_t e = cudaGraphAddMemsetNode(&nd, g, nullptr, 0, &mp);
+    clears.push_back(nd);
+    return e;
+  };
+  GX_CUDA(add_memset(ctl, sizeof(Ctl) / 4));
+  const uint64_t words = (uint64_t)P.B * P.nb;
+  constexpr uint64_t kPiece = 1ull << 30;  // words per memset node
+  for (uint64_t w0 = 0; w0 < words; w0 += kPiece) GX_CUDA(add_memset(table + w0, std::min(kPiece, words - w0)));
+  auto add_kernel = [&](cudaGraph_t gr, const cudaGraphNode_t* deps, size_t nd, const void* fn, dim3 gd, dim3 bd,
+                        size_t sh, void** args, cudaGraphNode_t* out) -> cudaError_t {
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(fn);
+    kp.gridDim = gd;
+    kp.blockDim = bd;
+    kp.sharedMemBytes = (unsigned)sh;
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, gr, deps, nd, &kp);
+  };
+  InitArgs ia_c = ia;
+  ExpandArgs eg_c = eg;
+  void* args_i[] = {&ia_c};
+  void* args_l[] = {&la};
+  void* args_e[] = {&eg_c};
+  cudaGraphNode_t init, start, ex, adv;
+  GX_CUDA(add_kernel(g, clears.data(), clears.size(), P.ks->init_fn, dim3(1), dim3(32), 0, args_i, &init));
+  GX_CUDA(add_kernel(g, &init, 1, reinterpret_cast<const void*>(&gxd::loop_start_kernel), dim3(1), dim3(1), 0,
+                     args_l, &start));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  GX_CUDA(cudaGraphAddNode(&cnode, g, &start, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  GX_CUDA(add_kernel(body, nullptr, 0, P.ks->expand_fn, dim3((unsigned)grid), dim3(kBlock), smem, args_e, &ex));
+  GX_CUDA(add_kernel(body, &ex, 1, reinterpret_cast<const void*>(&gxd::level_advance_kernel), dim3(1), dim3(1), 0,
+                     args_l, &adv));
+  cudaGraphExec_t exec;
+  GX_CUDA(cudaGraphInstantiate(&exec, g, 0));
+  h->loop_exec = exec;
   return GX_OK;
 }
 
@@ -293,9 +457,13 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
     }
   } evfree{ev0, ev1, ek0, ek1};
 
+  // levels on the device unless asked otherwise; the partitioned path needs the host
+  const bool device_loop = !o->host_loop && P.logp == 0;
   GX_CUDA(cudaEventRecord(ev0, st));
-  GX_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
-  GX_CUDA(cudaMemsetAsync(table, 0, 4ull * P.B * P.nb, st));
+  if (!device_loop) {
+    GX_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
+    GX_CUDA(cudaMemsetAsync(table, 0, 4ull * P.B * P.nb, st));
+  }
 
   InitArgs ia{};
   hash_multipliers(ia.muls.m, kMaxRounds);
@@ -305,7 +473,7 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   ia.frontier = front;
   ia.ctl = ctl;
   for (int w = 0; w < 4; ++w) ia.vec[w] = net.init_vec[w];
-  GX_CUDA(P.ks->init(ia, st));
+  if (!device_loop) GX_CUDA(P.ks->init(ia, st));
 
   ExpandArgs ea{};
   ea.blob = blob;
@@ -362,7 +530,62 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   std::vector<double> lv_ms;
   std::vector<uint64_t> lv_probes, lv_trans;
   uint64_t prev_probes = 0, prev_trans = 0;
-  bool complete = false;
+  bool complete = false, finished = false;
+  uint64_t kernel_launches = device_loop ? 0 : 1, device_levels = 0, d2h_loop = 0;
+  if (device_loop) {
+    LoopArgs la{};
+    la.ctl = ctl;
+    unsigned long long* lv = reinterpret_cast<unsigned long long*>(base + P.off_loop);
+    la.lv_size = lv;
+    la.lv_tns = lv + kLoopLevels;
+    la.lv_probes = lv + 2 * kLoopLevels;
+    la.lv_trans = lv + 3 * kLoopLevels;
+    la.cap = kLoopLevels;
+    la.stop_dl = stop_first ? 1 : 0;
+    la.stop_viol = stop_viol ? 1 : 0;
+    la.max_levels = o->max_levels;
+    ExpandArgs eg = ea;
+    eg.dev_range = 1;
+    // the graph holds every argument by value: rebuild it when anything changes
+    std::vector<unsigned char> key(sizeof(gx_explore_opts) + 5 * sizeof(uint64_t));
+    const uint64_t extra[5] = {reinterpret_cast<uint64_t>(ws), P.total, stop_first ? 1ull : 0ull, smem, max_grid};
+    std::memcpy(key.data(), o, sizeof(gx_explore_opts));
+    std::memcpy(key.data() + sizeof(gx_explore_opts), extra, sizeof(extra));
+    if (!h->loop_exec || h->loop_key != key) {
+      s = build_loop_graph(h, P, ctl, table, ia, eg, la, smem, max_grid);
+      if (s != GX_OK) return s;
+      h->loop_key = key;
+    }
+    GX_CUDA(cudaGraphLaunch(static_cast<cudaGraphExec_t>(h->loop_exec), st));
+    GX_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    std::vector<unsigned long long> hl(4ull * kLoopLevels);
+    GX_CUDA(cudaMemcpyAsync(hl.data(), lv, 8ull * hl.size(), cudaMemcpyDeviceToHost, st));
+    GX_CUDA(cudaStreamSynchronize(st));
+    d2h_loop = sizeof(Ctl) + 8ull * hl.size();
+    const uint64_t nd = hc->levels_done;
+    const uint64_t nl = std::min<uint64_t>(hc->n_levels, kLoopLevels);
+    levels.assign(hl.begin(), hl.begin() + nl);
+    for (uint64_t k = 0; k < nd && k < kLoopLevels; ++k) {
+      lv_ms.push_back(1e-6 * (double)hl[kLoopLevels + k]);
+      lv_probes.push_back(hl[2 * kLoopLevels + k] - prev_probes);
+      lv_trans.push_back(hl[3 * kLoopLevels + k] - prev_trans);
+      prev_probes = hl[2 * kLoopLevels + k];
+      prev_trans = hl[3 * kLoopLevels + k];
+      expand_ms += lv_ms.back();
+    }
+    explored = hc->explored;
+    levels_done = nd;
+    launches = nd;
+    device_levels = nd;
+    kernel_launches = 2 + 2 * nd;  // init, start, then expand + advance per level
+    first_dl = hc->first_dl;
+    first_viol = hc->first_viol;
+    complete = hc->complete != 0;
+    err = hc->error;
+    cur_begin = hc->cur_begin;
+    cur_end = hc->cur_end;
+    finished = !hc->yielded;
+  }
   // partitioned path set-up
   PartArgs pa{};
   size_t psmem = 0;
@@ -383,7 +606,7 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   }
   uint64_t part_levels = 0, d2h_tot = 0;
 
-  while (true) {
+  while (!finished) {
     const uint64_t F = cur_end - cur_begin;
     ea.cur_begin = cur_begin;
     ea.cur_end = cur_end;
@@ -514,10 +737,12 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   S.gpu_ms = total_ms;
   S.expand_ms = expand_ms;
   S.expand_launches = launches;
+  S.kernel_launches = kernel_launches + (launches - device_levels);
+  S.device_levels = device_levels;
   S.probes = hc->probes;
   S.partitioned_levels = part_levels;
   S.h2d_bytes = 4ull * net.blob.size();
-  S.d2h_bytes = sizeof(Ctl) * levels_done + 4ull * (dlw.size() + viw.size()) + d2h_tot;
+  S.d2h_bytes = sizeof(Ctl) * (levels_done - device_levels) + d2h_loop + 4ull * (dlw.size() + viw.size()) + d2h_tot;
   h->levels = levels;
   h->level_ms = lv_ms;
   h->level_probes = lv_probes;

@@ -72,6 +72,18 @@ struct gx_net {
   std::vector<uint32_t> guided_trace;
   // label names of a network read from text (gx_load_exp); empty otherwise
   std::vector<std::string> label_names;
+  // cached executable graph of the device-driven level loop (CUDA objects kept
+  // opaque here), the key it was built for, and the function that frees it
+  void* loop_graph = nullptr;
+  void* loop_exec = nullptr;
+  std::vector<unsigned char> loop_key;
+  void (*release)(gx_net*) = nullptr;
+  gx_net() = default;
+  gx_net(const gx_net&) = delete;
+  gx_net& operator=(const gx_net&) = delete;
+  ~gx_net() {
+    if (release) release(this);
+  }
 };
 
 namespace gx {

@@ -362,6 +362,16 @@ __device__ __forceinline__ void insert_lanes(const Target& a, const uint64_t* mu
 template <int W, int B, int G>
 __global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(const gx::ExpandArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
+  // the level being expanded: from the parameters, or (device-driven level
+  // loop) from the control block the previous level's advance step wrote
+  uint64_t cur_begin = a.cur_begin, cur_end = a.cur_end;
+  if (a.dev_range) {
+    cur_begin = a.ctl->cur_begin;
+    cur_end = a.ctl->cur_end;
+    // a fixed full-size grid: CTAs beyond the level's first chunks leave at once
+    const uint64_t per_cta = 32ull * (gx::kBlock / 32);
+    if ((uint64_t)blockIdx.x * per_cta >= cur_end - cur_begin) return;
+  }
   const uint64_t* muls;
   const uint32_t* t = stage_tables(sm, a.muls, a.rounds, a.blob, a.blob_words, a.stage, muls);
   __syncthreads();
@@ -372,7 +382,8 @@ __global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(
   uint32_t probes = 0, err = 0;
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
-  const Target tg = target_of(a);
+  Target tg = target_of(a);
+  tg.cur_begin = cur_begin;
   WarpCache cache{nullptr, 0};
   if (W <= 2 && a.cache_log2 > 0) {
     uint32_t* cbase = sm + 2 * kMaxRounds + (a.stage ? a.blob_words : 0);
@@ -387,10 +398,10 @@ __global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(
     unsigned long long chunk = 0;
     if (lane == 0) chunk = atomicAdd(&a.ctl->claim, 32ull);
     chunk = __shfl_sync(FULLMASK, chunk, 0);
-    const uint64_t start = a.cur_begin + chunk;
-    if (start >= a.cur_end) break;
+    const uint64_t start = cur_begin + chunk;
+    if (start >= cur_end) break;
     const uint64_t idx = start + lane;
-    const bool valid = idx < a.cur_end;
+    const bool valid = idx < cur_end;
     uint32_t v[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) v[w] = 0;
@@ -739,7 +750,8 @@ const KernelSet* kernel_set() {
                             reinterpret_cast<const void*>(&gxd::fop_kernel<W, B, G>),
                             reinterpret_cast<const void*>(&gxd::part_count_kernel<W>),
                             reinterpret_cast<const void*>(&gxd::part_scatter_kernel<W>),
-                            reinterpret_cast<const void*>(&gxd::part_probe_kernel<W, B, G>)};
+                            reinterpret_cast<const void*>(&gxd::part_probe_kernel<W, B, G>),
+                            reinterpret_cast<const void*>(&gxd::init_kernel<W, B, G>)};
   return &ks;
 }
 

@@ -25,6 +25,14 @@ struct Ctl {
   unsigned int pad;
   unsigned long long digest[3];    // gx_set_digest: count, sum, xor
   unsigned long long viol_count, viol_sum, viol_xor;  // safety check
+  // device-driven level loop: the level to expand next and the loop's bookkeeping
+  unsigned long long cur_begin, cur_end;
+  unsigned long long n_levels;      // entries of the level-size list (level 0 included)
+  unsigned long long levels_done;   // levels expanded
+  unsigned long long explored;
+  unsigned long long t_prev;        // %globaltimer (ns) at the end of the previous level
+  long long first_dl, first_viol;   // level of the first deadlock / violation, -1 if none
+  unsigned int complete, yielded;   // the frontier ran empty / the level arrays filled up
 };
 static_assert(sizeof(Ctl) <= 256, "control block");
 
@@ -54,6 +62,7 @@ struct ExpandArgs {
   uint32_t watch_word, watch_shift, watch_mask, watch_value;
   uint32_t* viol_buf;        // violating vectors, W words each
   uint32_t viol_cap;
+  int dev_range;             // 1: read cur_begin / cur_end from the control block
 };
 
 // Partitioned expansion of one level (or one batch of it): successors are
@@ -111,6 +120,7 @@ struct KernelSet {
   const void* part_count_fn;
   const void* part_scatter_fn;
   const void* part_probe_fn;
+  const void* init_fn;    // for graph kernel nodes
 };
 
 // Kernels for slot width W, bucket words B and group lanes G; nullptr if the

@@ -55,7 +55,8 @@ class gx_explore_opts(ctypes.Structure):
                 ("frontier_states", u64), ("successor_buffer", u64), ("slice_log2", u32),
                 ("partition_min_states", u32), ("guided_bins", u32), ("warp_cache_log2", u32),
                 ("guided_scale", ctypes.c_float), ("watch", u32), ("watch_proc", u32),
-                ("watch_state", u32), ("stop_at_first_violation", u32), ("violation_cap", u32)]
+                ("watch_state", u32), ("stop_at_first_violation", u32), ("violation_cap", u32),
+                ("host_loop", u32)]
 
 
 MLP_IN, MLP_HIDDEN = 16, 128
@@ -76,7 +77,8 @@ class gx_stats_t(ctypes.Structure):
                 ("expand_ms", ctypes.c_double), ("expand_launches", u64), ("probes", u64),
                 ("h2d_bytes", u64), ("d2h_bytes", u64), ("partitioned_levels", u64),
                 ("violation_count", u64), ("violation_sum", u64), ("violation_xor", u64),
-                ("first_violation_level", ctypes.c_int64)]
+                ("first_violation_level", ctypes.c_int64), ("kernel_launches", u64),
+                ("device_levels", u64)]
 
 
 class gx_batch_opts(ctypes.Structure):

@@ -270,3 +270,53 @@ def test_producer_consumers_family(cuda, k):
     assert s["states"] == 2 ** (k + 1)
     assert s["transitions"] == 2 ** k + k * 2 ** (k - 1) + k * 2 ** (k + 1)
     assert s["deadlock_count"] == 0 and s["complete"] == 1
+
+
+def _chain(n):
+    """One process walking a path of n local states: n BFS levels, the last state a deadlock."""
+    return inputs.Network(1, [inputs.LTS(n, 0, [(i, 0, i + 1) for i in range(n - 1)])], [],
+                          name=f"chain_{n}")
+
+
+@pytest.mark.parametrize("n", [4095, 4096, 4097, 6000])
+def test_device_loop_hands_over_to_the_host_after_4096_levels(cuda, n):
+    """The device-driven level loop records 4096 levels at most; the host loop
+    carries on from there with the same results."""
+    s = assert_parity(_chain(n), table_bytes=1 << 20)
+    assert s["n_levels"] == n and s["first_deadlock_level"] == n - 1
+    assert s["device_levels"] == min(n, 4095)
+    assert len(gx.level_profile(run_gpu(_chain(n), table_bytes=1 << 20)[0])["ms"]) == n
+
+
+@pytest.mark.parametrize("net", [inputs.token_ring(7), inputs.random_network(6, 8, 8, 0, 2, 10, n_sync=4, parties=2),
+                                 inputs.random_network(0, 13, 64, 1, 3, 16, n_sync=8, parties=3, cluster=4)],
+                         ids=lambda n: n.name)
+def test_host_and_device_level_loops_agree(cuda, net):
+    h1, s1, lv1, _ = run_gpu(net, table_bytes=1 << 24)
+    h2, s2, lv2, _ = run_gpu(net, table_bytes=1 << 24, host_loop=1)
+    assert s1["device_levels"] == s1["n_levels"] and s2["device_levels"] == 0
+    assert lv1 == lv2
+    # bucket reads are not compared: warp-cache hits depend on which warp takes which state
+    for k in ("states", "transitions", "explored", "deadlock_count", "deadlock_sum", "deadlock_xor",
+              "first_deadlock_level", "complete"):
+        assert s1[k] == s2[k], k
+    p1, p2 = gx.level_profile(h1), gx.level_profile(h2)
+    assert p1["transitions"] == p2["transitions"] and len(p1["ms"]) == len(p2["ms"])
+    assert s1["kernel_launches"] == 2 + 2 * s1["expand_launches"]
+    assert s2["kernel_launches"] == 1 + s2["expand_launches"]
+
+
+def test_device_loop_max_levels_and_repeated_graph_launches(cuda):
+    """max_levels stops the device loop; the cached graph is rebuilt when the
+    options change and reused when they do not."""
+    net = inputs.token_ring(8)
+    r = oracle.explore(net)
+    for lim in (1, 5, 20):
+        _, s, lv, _ = run_gpu(net, table_bytes=1 << 22, max_levels=lim)
+        assert s["explored"] == sum(r.levels[:lim]) and lv == r.levels[:lim + 1]
+    h = gx.load_network(net)
+    o = gx.default_opts(table_bytes=1 << 22)
+    ws = gx.alloc_workspace(h, o)
+    for _ in range(3):
+        gx.explore(h, o, ws)
+        assert gx.stats(h)["states"] == r.states
