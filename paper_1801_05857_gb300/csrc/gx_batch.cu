@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(gx::kBlock) batch_expand_kernel(const BatchArg
     }
     const uint32_t* t = b.blob;
     const NetBlobLayout L = b.lay;
-    const Target tg{b.table, b.log2nb, a.rounds, &b.next_end, b.frontier, b.fmask, b.cur_begin};
+    const Target tg{b.table, b.log2nb, a.rounds, &b.next_end, b.frontier, b.fmask, b.cur_begin};  // per network
     const uint64_t first = b.cur_begin + (c - __ldcg(a.prefix + lo)) * (uint64_t)a.chunk;
     const uint64_t end = b.cur_end;
     unsigned long long trans = 0;

@@ -57,10 +57,14 @@ __device__ __forceinline__ uint32_t count_succ(const uint32_t* t, const NetBlobL
 // Resumable enumeration of the successors of one vector: first the local
 // edges process by process, then each enabled rule's combinations in
 // mixed-radix order.  next() must be called at most count_succ() times.
+// The two phases share the iterator's four words (it keeps register use low
+// in the level kernel): idx counts processes 0..n_procs-1 and then rules
+// (n_procs + r); [e, e_end) is the current process's delta range, or the
+// current rule's combination counter and count; wd is the current process's
+// word, or the current rule.
 struct SuccIter {
-  uint32_t p, e, e_end, wd;  // local phase
-  uint32_t r, cur, k, k_end; // rule phase
-  __device__ __forceinline__ void init() { p = e = e_end = wd = r = cur = k = k_end = 0; }
+  uint32_t idx, e, e_end, wd;
+  __device__ __forceinline__ void init() { idx = e = e_end = wd = 0; }
 };
 
 template <int W>
@@ -68,20 +72,22 @@ __device__ __forceinline__ void next_succ(SuccIter& it, const uint32_t* t, const
                                           const uint32_t (&v)[W], uint32_t (&out)[W]) {
 #pragma unroll
   for (int w = 0; w < W; ++w) out[w] = v[w];
-  while (it.e == it.e_end && it.p < L.n_procs) {
-    const uint32_t p = it.p++;
-    const uint32_t* o = class_range(t, L, p, local_state<W>(t, L, v, p));
-    it.e = o[0];
-    it.e_end = o[1];
-    it.wd = t[L.proc_word + p];
+  if (it.idx <= L.n_procs) {  // local phase (or its end)
+    while (it.e == it.e_end && it.idx < L.n_procs) {
+      const uint32_t p = it.idx++;
+      const uint32_t* o = class_range(t, L, p, local_state<W>(t, L, v, p));
+      it.e = o[0];
+      it.e_end = o[1];
+      it.wd = t[L.proc_word + p];
+    }
+    if (it.e < it.e_end) {
+      xor_at<W>(out, it.wd, t[L.cdelta + it.e]);
+      ++it.e;
+      return;
+    }
   }
-  if (it.e < it.e_end) {
-    xor_at<W>(out, it.wd, t[L.cdelta + it.e]);
-    ++it.e;
-    return;
-  }
-  while (it.k == it.k_end && it.r < L.n_rules) {
-    const uint32_t r = it.r++;
+  while (it.e == it.e_end && it.idx < L.n_procs + L.n_rules) {
+    const uint32_t r = it.idx++ - L.n_procs;
     uint32_t prod = 1;
     const uint32_t j1 = t[L.rule_off + r + 1];
     for (uint32_t j = t[L.rule_off + r]; j < j1 && prod; ++j) {
@@ -89,19 +95,22 @@ __device__ __forceinline__ void next_succ(SuccIter& it, const uint32_t* t, const
       const uint32_t* o = class_range(t, L, c, local_state<W>(t, L, v, t[L.cls_proc + c]));
       prod *= o[1] - o[0];
     }
-    it.cur = r;
-    it.k = 0;
-    it.k_end = prod;
+    it.wd = r;
+    it.e = 0;
+    it.e_end = prod;
   }
-  uint32_t x = it.k++;
-  const uint32_t j1 = t[L.rule_off + it.cur + 1];
-  for (uint32_t j = t[L.rule_off + it.cur]; j < j1; ++j) {
+  uint32_t x = it.e++;
+  const uint32_t j1 = t[L.rule_off + it.wd + 1];
+  for (uint32_t j = t[L.rule_off + it.wd]; j < j1; ++j) {
     const uint32_t c = t[L.rule_cls + j];
     const uint32_t p = t[L.cls_proc + c];
     const uint32_t* o = class_range(t, L, c, local_state<W>(t, L, v, p));
     const uint32_t cnt = o[1] - o[0];
-    const uint32_t i = x % cnt;
-    x /= cnt;
+    uint32_t i = 0;
+    if (cnt > 1) {  // one matching edge is the common case: no division
+      i = x % cnt;
+      x /= cnt;
+    }
     xor_at<W>(out, t[L.proc_word + p], t[L.cdelta + o[0] + i]);
   }
 }
@@ -187,19 +196,37 @@ __device__ __forceinline__ const uint32_t* stage_tables(uint32_t* sm, const gx::
 }
 
 // Where find-or-put inserts and where new vectors go: one network's table and
-// frontier ring (the level being expanded starts at cur_begin).
+// frontier ring (the level being expanded starts at begin()).  Target holds
+// the values (the batched kernel loads them per network); ParamTarget reads
+// them from the single-network kernel's parameters, which live in the
+// constant bank and so take no registers in the inner loop.
 struct Target {
-  uint32_t* table;
-  int log2nb, rounds;
-  unsigned long long* next_end;
-  uint32_t* frontier;
-  uint64_t fmask;
+  uint32_t* tab;
+  int l2nb, nrounds;
+  unsigned long long* nend;
+  uint32_t* front;
+  uint64_t fm;
   uint64_t cur_begin;
+  __device__ __forceinline__ uint32_t* table() const { return tab; }
+  __device__ __forceinline__ int log2nb() const { return l2nb; }
+  __device__ __forceinline__ int rounds() const { return nrounds; }
+  __device__ __forceinline__ unsigned long long* next_end() const { return nend; }
+  __device__ __forceinline__ uint32_t* frontier() const { return front; }
+  __device__ __forceinline__ uint64_t fmask() const { return fm; }
+  __device__ __forceinline__ uint64_t begin() const { return cur_begin; }
 };
 
-__device__ __forceinline__ Target target_of(const gx::ExpandArgs& a) {
-  return Target{a.table, a.log2nb, a.rounds, &a.ctl->next_end, a.frontier, a.fmask, a.cur_begin};
-}
+struct ParamTarget {
+  const gx::ExpandArgs& a;
+  const unsigned long long* range;  // [begin, end) of the level, in shared memory
+  __device__ __forceinline__ uint32_t* table() const { return a.table; }
+  __device__ __forceinline__ int log2nb() const { return a.log2nb; }
+  __device__ __forceinline__ int rounds() const { return a.rounds; }
+  __device__ __forceinline__ unsigned long long* next_end() const { return &a.ctl->next_end; }
+  __device__ __forceinline__ uint32_t* frontier() const { return a.frontier; }
+  __device__ __forceinline__ uint64_t fmask() const { return a.fmask; }
+  __device__ __forceinline__ uint64_t begin() const { return range[0]; }
+};
 
 // Per-warp staging of new vectors in shared memory: lanes that inserted a
 // vector append it here (ballot + popc, no atomic); every 32 staged vectors
@@ -211,24 +238,24 @@ struct WarpStage {
   uint32_t* buf;  // kStage * W words of this warp
   int n;          // staged vectors (uniform in the warp)
 
-  template <int W>
-  __device__ __forceinline__ void write_out(const Target& a, int m, uint32_t& err) {
+  template <int W, class T>
+  __device__ __forceinline__ void write_out(const T& a, int m, uint32_t& err) {
     const int lane = threadIdx.x & 31;
     unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(a.next_end, (unsigned long long)m);
+    if (lane == 0) base = atomicAdd(a.next_end(), (unsigned long long)m);
     base = __shfl_sync(FULLMASK, base, 0);
     if (lane < m) {
       const uint64_t pos = base + lane;
       uint32_t v[W];
 #pragma unroll
       for (int w = 0; w < W; ++w) v[w] = buf[lane * W + w];
-      if (pos - a.cur_begin <= a.fmask) store_vec<W>(a.frontier + (pos & a.fmask) * W, v);
+      if (pos - a.begin() <= a.fmask()) store_vec<W>(a.frontier() + (pos & a.fmask()) * W, v);
       else err |= gx::ERR_FRONTIER;
     }
   }
 
-  template <int W>
-  __device__ __forceinline__ void push(const Target& a, bool ins, const uint32_t (&v)[W],
+  template <int W, class T>
+  __device__ __forceinline__ void push(const T& a, bool ins, const uint32_t (&v)[W],
                                        uint32_t& err) {
     const int lane = threadIdx.x & 31;
     const uint32_t im = __ballot_sync(FULLMASK, ins);
@@ -252,8 +279,8 @@ struct WarpStage {
     }
   }
 
-  template <int W>
-  __device__ __forceinline__ void flush(const Target& a, uint32_t& err) {
+  template <int W, class T>
+  __device__ __forceinline__ void flush(const T& a, uint32_t& err) {
     __syncwarp();
     if (n > 0) write_out<W>(a, n, err);
     n = 0;
@@ -305,8 +332,8 @@ struct PerLane {
 // the full find-or-put with the CAS and further rounds).  Vectors this call
 // inserted go to the warp's staging buffer.
 // Must be called by all 32 lanes of the warp together.
-template <int W, int B, int G, int K>
-__device__ __forceinline__ void insert_lanes(const Target& a, const uint64_t* muls,
+template <int W, int B, int G, int K, class T>
+__device__ __forceinline__ void insert_lanes(const T& a, const uint64_t* muls,
                                              const Group<G>& g, const bool (&has)[K],
                                              const uint32_t (&s)[K][W], uint32_t& probes,
                                              uint32_t& err, WarpStage& st,
@@ -335,8 +362,8 @@ __device__ __forceinline__ void insert_lanes(const Target& a, const uint64_t* mu
         if (cache.base && cache.template seen<W>(hh, x[j])) hv[j] = false;
       }
       if (hv[j]) {
-        const uint64_t b = bucket_of(vec_hash<W>(x[j]), muls[0], a.log2nb);
-        load_words<LW>(a.table + b * (uint64_t)B + (uint64_t)g.glane * LW, pre[j]);
+        const uint64_t b = bucket_of(vec_hash<W>(x[j]), muls[0], a.log2nb());
+        load_words<LW>(a.table() + b * (uint64_t)B + (uint64_t)g.glane * LW, pre[j]);
         probes += g.glane == 0;
       }
     }
@@ -344,7 +371,7 @@ __device__ __forceinline__ void insert_lanes(const Target& a, const uint64_t* mu
     for (int j = 0; j < CH; ++j) {
       if (!hv[j]) continue;
       const int i = c + j;
-      const int r = find_or_put_from<W, B, G, true>(a.table, a.log2nb, a.rounds, muls, x[j], g, probes,
+      const int r = find_or_put_from<W, B, G, true>(a.table(), a.log2nb(), a.rounds(), muls, x[j], g, probes,
                                                     pre[j]);
       if (r == FOP_FULL) err |= gx::ERR_TABLE_FULL;
       if (g.glane == i / K && r == FOP_INSERTED) inserted[i % K] = true;
@@ -355,22 +382,36 @@ __device__ __forceinline__ void insert_lanes(const Target& a, const uint64_t* mu
 }
 
 // Resident CTAs per SM the level kernel is compiled for (register budget).
-#ifndef GX_EXPAND_MIN_CTAS
-#define GX_EXPAND_MIN_CTAS 5
-#endif
+// A lane holds min(G, 4) first buckets in flight of B / G words each; up to
+// 8 such words of 1- or 2-word slots fit 48 registers (5 CTAs), up to 16 fit
+// 64 (4 CTAs), more get 85 (3 CTAs); 4-word slots with 4 or more lanes per
+// bucket also get 3.  (Checked with -Xptxas -v: at most a few bytes spill.)
+template <int W, int B, int G>
+struct ExpandOcc {
+  static constexpr int inflight = (G < 4 ? G : 4) * (B / G);
+  static constexpr int min_ctas =
+      (W <= 2 && inflight <= 8) ? 5 : ((inflight <= 16 && !(W == 4 && G >= 4)) ? 4 : 3);
+};
 
 template <int W, int B, int G>
-__global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(const gx::ExpandArgs a) {
+__global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expand_kernel(const gx::ExpandArgs a) {
   extern __shared__ __align__(16) uint32_t sm[];
   // the level being expanded: from the parameters, or (device-driven level
-  // loop) from the control block the previous level's advance step wrote
-  uint64_t cur_begin = a.cur_begin, cur_end = a.cur_end;
+  // loop) from the control block the previous level's advance step wrote.
+  // Kept in shared memory, not registers, for the inner loop's sake.
+  __shared__ unsigned long long s_range[2];
   if (a.dev_range) {
-    cur_begin = a.ctl->cur_begin;
-    cur_end = a.ctl->cur_end;
+    const uint64_t b0 = a.ctl->cur_begin, e0 = a.ctl->cur_end;
     // a fixed full-size grid: CTAs beyond the level's first chunks leave at once
     const uint64_t per_cta = 32ull * (gx::kBlock / 32);
-    if ((uint64_t)blockIdx.x * per_cta >= cur_end - cur_begin) return;
+    if ((uint64_t)blockIdx.x * per_cta >= e0 - b0) return;
+    if (threadIdx.x == 0) {
+      s_range[0] = b0;
+      s_range[1] = e0;
+    }
+  } else if (threadIdx.x == 0) {
+    s_range[0] = a.cur_begin;
+    s_range[1] = a.cur_end;
   }
   const uint64_t* muls;
   const uint32_t* t = stage_tables(sm, a.muls, a.rounds, a.blob, a.blob_words, a.stage, muls);
@@ -378,12 +419,11 @@ __global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(
   const NetBlobLayout& L = a.lay;
   const int lane = threadIdx.x & 31;
   const Group<G> g;
-  unsigned long long trans = 0;
+  uint32_t trans = 0;  // per thread and launch: far below 2^32
   uint32_t probes = 0, err = 0;
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
-  Target tg = target_of(a);
-  tg.cur_begin = cur_begin;
+  const ParamTarget tg{a, s_range};
   WarpCache cache{nullptr, 0};
   if (W <= 2 && a.cache_log2 > 0) {
     uint32_t* cbase = sm + 2 * kMaxRounds + (a.stage ? a.blob_words : 0);
@@ -398,10 +438,10 @@ __global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(
     unsigned long long chunk = 0;
     if (lane == 0) chunk = atomicAdd(&a.ctl->claim, 32ull);
     chunk = __shfl_sync(FULLMASK, chunk, 0);
-    const uint64_t start = cur_begin + chunk;
-    if (start >= cur_end) break;
+    const uint64_t start = s_range[0] + chunk;
+    if (start >= s_range[1]) break;
     const uint64_t idx = start + lane;
-    const bool valid = idx < cur_end;
+    const bool valid = idx < s_range[1];
     uint32_t v[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) v[w] = 0;
@@ -437,11 +477,11 @@ __global__ void __launch_bounds__(gx::kBlock, GX_EXPAND_MIN_CTAS) expand_kernel(
     }
   }
   st.flush<W>(tg, err);
-  trans = warp_sum(trans);
+  const unsigned long long trans_w = warp_sum((unsigned long long)trans);
   const unsigned long long pr = warp_sum((unsigned long long)probes);
   err = __reduce_or_sync(FULLMASK, err);
   if (lane == 0) {
-    if (trans) atomicAdd(&a.ctl->transitions, trans);
+    if (trans_w) atomicAdd(&a.ctl->transitions, trans_w);
     if (pr) atomicAdd(&a.ctl->probes, pr);
     if (err) atomicOr(&a.ctl->error, err);
   }
@@ -614,7 +654,13 @@ __global__ void __launch_bounds__(gx::kBlock) part_probe_kernel(const gx::Expand
   uint32_t probes = 0, err = 0;
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
-  const Target tg = target_of(a);
+  __shared__ unsigned long long s_range[2];
+  if (threadIdx.x == 0) {
+    s_range[0] = a.cur_begin;
+    s_range[1] = a.cur_end;
+  }
+  __syncthreads();
+  const ParamTarget tg{a, s_range};
   while (true) {
     unsigned long long chunk = 0;
     if (lane == 0) chunk = atomicAdd(&a.ctl->claim, 32ull);
