@@ -62,25 +62,24 @@ __device__ __forceinline__ float block_sum128(float v, float* red) {
   return t;
 }
 
-// Forward (and, with GRAD, backward) of EPB examples per CTA; thread k owns
-// hidden unit k.  Gradients of the mean loss over n examples are added to g.
-template <bool GRAD>
-__global__ void __launch_bounds__(H) mlp_kernel(const float* __restrict__ p, const uint8_t* __restrict__ hist,
-                                                const float* __restrict__ label, uint64_t n,
-                                                const uint64_t* __restrict__ index, float inv_n,
-                                                float* __restrict__ out, float* __restrict__ g,
-                                                float* __restrict__ loss) {
+// Forward and backward of EPB examples per CTA on the CUDA cores; thread k
+// owns hidden unit k.  Gradients of the mean loss over n examples are added
+// to g, and the mean loss to *loss.
+__global__ void __launch_bounds__(H) grad_kernel(const float* __restrict__ p, const uint8_t* __restrict__ hist,
+                                                 const float* __restrict__ label, uint64_t n,
+                                                 const uint64_t* __restrict__ index, float inv_n,
+                                                 float* __restrict__ g, float* __restrict__ loss) {
   extern __shared__ float sm[];
   float* W2 = sm;                 // [H][LD2]
-  float* gW2 = W2 + H * LD2;      // [H][LD2] (GRAD only)
-  float* h1 = (GRAD ? gW2 + H * LD2 : W2 + H * LD2);  // [H]
+  float* gW2 = W2 + H * LD2;      // [H][LD2]
+  float* h1 = gW2 + H * LD2;      // [H]
   float* dh2 = h1 + H;            // [H]
   float* x = dh2 + H;             // [IN]
   float* red = x + IN;            // [4]
   const int k = threadIdx.x;
   for (int i = k; i < H * H; i += H) {
     W2[(i / H) * LD2 + (i % H)] = bf(p[OFF_W2 + i]);
-    if (GRAD) gW2[(i / H) * LD2 + (i % H)] = 0.f;
+    gW2[(i / H) * LD2 + (i % H)] = 0.f;
   }
   float w1[IN];
 #pragma unroll
@@ -113,10 +112,6 @@ __global__ void __launch_bounds__(H) mlp_kernel(const float* __restrict__ p, con
     for (int j = 0; j < H; ++j) a2 += W2[k * LD2 + j] * h1[j];
     const float z2 = fmaxf(a2, 0.f);
     const float y = block_sum128(w3 * z2, red) + b3;
-    if (!GRAD) {
-      if (k == 0) out[ex] = y;
-      continue;
-    }
     const float dy = 2.f * (y - label[ex]) * inv_n;
     if (k == 0) lsum += (y - label[ex]) * (y - label[ex]) * inv_n;
     gb3 += dy;
@@ -134,7 +129,6 @@ __global__ void __launch_bounds__(H) mlp_kernel(const float* __restrict__ p, con
     for (int i = 0; i < IN; ++i) gw1[i] += d1 * x[i];
     __syncthreads();
   }
-  if (!GRAD) return;
   __syncthreads();
   for (int i = k; i < H * H; i += H) atomicAdd(&g[OFF_W2 + i], gW2[(i / H) * LD2 + (i % H)]);
 #pragma unroll
@@ -201,7 +195,7 @@ __global__ void sample_kernel(uint64_t* __restrict__ idx, uint32_t batch, uint64
   idx[j] = (z ^ (z >> 31)) % n;
 }
 
-size_t smem_bytes(bool grad) { return sizeof(float) * ((grad ? 2 : 1) * H * LD2 + 2 * H + IN + 4); }
+constexpr size_t kGradSmemBytes = sizeof(float) * (2 * H * LD2 + 2 * H + IN + 4);
 
 }  // namespace gxm
 
@@ -216,8 +210,8 @@ namespace {
 gx_status set_smem() {
   static bool done = false;
   if (done) return GX_OK;
-  GM_CUDA(cudaFuncSetAttribute(gxm::mlp_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)gxm::smem_bytes(true)));
+  GM_CUDA(cudaFuncSetAttribute(gxm::grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)gxm::kGradSmemBytes));
   GM_CUDA(cudaFuncSetAttribute(gxm::mlp_tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)gxt::kTcSmemBytes));
   done = true;
@@ -291,8 +285,8 @@ gx_status gx_mlp_grad(const float* params, const uint8_t* hist, const float* lab
   GM_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * gxm::NPARAM, st));
   GM_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st));
   const uint64_t grid = (n + gxm::EPB - 1) / gxm::EPB;
-  gxm::mlp_kernel<true><<<(unsigned)grid, gxm::H, gxm::smem_bytes(true), st>>>(
-      params, hist, label, n, nullptr, 1.0f / (float)n, nullptr, grad, loss);
+  gxm::grad_kernel<<<(unsigned)grid, gxm::H, gxm::kGradSmemBytes, st>>>(params, hist, label, n, nullptr,
+                                                                       1.0f / (float)n, grad, loss);
   GM_CUDA(cudaGetLastError());
   return GX_OK;
 }
@@ -318,9 +312,8 @@ gx_status gx_mlp_train(float* params, float* state, const uint8_t* hist, const f
     b1t *= 0.9;
     b2t *= 0.999;
     gxm::sample_kernel<<<(batch + 255) / 256, 256, 0, st>>>(idx, batch, n, seed, t);
-    gxm::mlp_kernel<true><<<grid, gxm::H, gxm::smem_bytes(true), st>>>(params, hist, label, batch, idx,
-                                                                       1.0f / (float)batch, nullptr, g,
-                                                                       loss + t);
+    gxm::grad_kernel<<<grid, gxm::H, gxm::kGradSmemBytes, st>>>(params, hist, label, batch, idx,
+                                                                1.0f / (float)batch, g, loss + t);
     gxm::adam_kernel<<<(gxm::NPARAM + 255) / 256, 256, 0, st>>>(params, m, v, g, lr, (float)b1t, (float)b2t);
   }
   GM_CUDA(cudaGetLastError());
