@@ -58,10 +58,11 @@ def parse():
     ap.add_argument("--no-table", action="store_true", help="skip the Sec. 5.1 find-or-put part")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided deadlock-search part")
-    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep", "scaled", "scaling-table"],
+    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep", "scaled", "scaling-table", "scorer"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
                          "exploration for every (bucket, group) size; scaled: one large token ring; "
                          "scaling-table: ring and producer/consumer families by size (Table 1); "
+                         "scorer: the tensor-core scoring kernel alone; "
                          "one JSON line per point")
     return ap.parse_args()
 
@@ -728,6 +729,12 @@ def run_experiment(args):
                     print(json.dumps({"experiment": "sec5.1 find-or-put", **pt}), flush=True)
                     group *= 2
             del keys
+    elif args.experiment == "scorer":
+        # the tensor-core scorer alone (weights from a seeded initialisation; speed does
+        # not depend on their values), 4M random histograms
+        p = torch.empty(gx.MLP_PARAMS, dtype=torch.float32, device="cuda")
+        gx.mlp_init(p, 1)
+        print(json.dumps({"experiment": "scorer", **scoring_rate(torch, gx, p)}), flush=True)
     elif args.experiment == "scaling-table":
         scaling_table(torch, gx, inputs, args)
     elif args.experiment == "scaled":

@@ -592,12 +592,12 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
   const size_t smem = a.stage ? blob_bytes : 0;
   GG_CUDA(cudaFuncSetAttribute(P.k.expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   GG_CUDA(cudaFuncSetAttribute(P.k.score, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gxt::kTcSmemBytes));
-  int per_sm = 0, score_per_sm = 0;
+  GG_CUDA(cudaFuncSetAttribute(P.k.score, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared));
+  int per_sm = 0;
   GG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.k.expand, kBlock, smem));
-  GG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&score_per_sm, P.k.score, gxt::kRows, gxt::kTcSmemBytes));
   const int grid = sms * std::max(per_sm, 1);
-  // each scoring CTA holds 128 of an SM's 512 TMEM columns
-  const int score_grid = sms * std::min(std::max(score_per_sm, 1), 4);
+  const int score_grid = sms * gxt::tc_ctas_per_sm(dev);
 
   cudaEvent_t e0, e1;
   GG_CUDA(cudaEventCreate(&e0));

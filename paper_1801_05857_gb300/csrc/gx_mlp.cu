@@ -214,6 +214,9 @@ gx_status set_smem() {
                                (int)gxm::kGradSmemBytes));
   GM_CUDA(cudaFuncSetAttribute(gxm::mlp_tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)gxt::kTcSmemBytes));
+  // all of the SM's unified L1/shared memory as shared memory, so that 3 tiles fit per SM
+  GM_CUDA(cudaFuncSetAttribute(gxm::mlp_tc_forward_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared));
   done = true;
   return GX_OK;
 }
@@ -255,14 +258,11 @@ gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, f
   gx_status s = set_smem();
   if (s != GX_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0;
   GM_CUDA(cudaGetDevice(&dev));
   GM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  GM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gxm::mlp_tc_forward_kernel, gxt::kRows,
-                                                        gxt::kTcSmemBytes));
-  // each CTA holds 128 of an SM's 512 TMEM columns
   const uint64_t tiles = (n + gxt::kRows - 1) / gxt::kRows;
-  const uint64_t grid = std::min<uint64_t>(tiles, (uint64_t)sms * std::min(std::max(per_sm, 1), 4));
+  const uint64_t grid = std::min<uint64_t>(tiles, (uint64_t)sms * gxt::tc_ctas_per_sm(dev));
   const unsigned int zero = 0;
   GM_CUDA(cudaMemcpyToSymbolAsync(gxm::g_tc_error, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st));
   gxm::mlp_tc_forward_kernel<<<(unsigned)grid, gxt::kRows, gxt::kTcSmemBytes, st>>>(params, hist, n, out);

@@ -27,6 +27,7 @@
 #include <cstdint>
 
 #include <cuda_bf16.h>
+#include <cuda_runtime.h>
 
 #include "gx.h"
 
@@ -159,6 +160,18 @@ struct __align__(1024) TcSmem {
   unsigned long long mbar;
 };
 constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;  // + alignment slack
+
+// Scoring CTAs per SM, from the device's shared memory (the occupancy query
+// reports 1 for these kernels): as many tiles as fit, at most 4 so that their
+// TMEM columns (128 each) never exceed the SM's 512.
+inline int tc_ctas_per_sm(int dev) {
+  int smem_sm = 0, reserved = 0;
+  if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess)
+    return 1;
+  const int n = smem_sm / (int)(kTcSmemBytes + (size_t)reserved);
+  return n < 1 ? 1 : (n > 4 ? 4 : n);
+}
 
 __device__ __forceinline__ TcSmem* tc_smem(void* dyn) {
   const uintptr_t p = (reinterpret_cast<uintptr_t>(dyn) + 1023) & ~uintptr_t(1023);
