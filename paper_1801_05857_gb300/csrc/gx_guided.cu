@@ -45,6 +45,8 @@ struct GuidedCtl {
   unsigned long long dl_count;
   unsigned long long claim;
   unsigned long long pending;    // new states appended by the current iteration's expansion
+  unsigned long long iters;      // iterations run
+  unsigned long long path_len;   // states on the deadlock's path (gx_guided_trace), 0 if none
 };
 
 struct GuidedArgs {
@@ -70,6 +72,8 @@ struct GuidedArgs {
   uint32_t* pend;                 // [pend_cap] entries of E words (vector, parent)
   uint64_t pend_cap;
   uint32_t init_vec[4];
+  cudaGraphConditionalHandle cond;  // device-driven iteration loop
+  unsigned long long max_iters;
 };
 
 constexpr unsigned int ERR_BINS = 16u, ERR_LOG = 32u, ERR_WIDE = 64u, ERR_PENDING = 128u;
@@ -441,6 +445,48 @@ __global__ void __launch_bounds__(gxt::kRows) guided_score_kernel(const GuidedAr
   if (err) atomicOr(&a.ctl->error, err);
 }
 
+// ---- the device-driven iteration loop and the deadlock's path
+
+// Control block at the start of a search (the rest was cleared).
+__global__ void guided_reset_kernel(const GuidedArgs a) { a.ctl->found = ~0ull; }
+
+__global__ void guided_loop_start_kernel(const GuidedArgs a) {
+  cudaGraphSetConditional(a.cond, a.ctl->error ? 0u : 1u);
+}
+
+// After {select, expand, score}: go on unless a deadlock was found, the open
+// set is empty, an error occurred or the iteration bound (every iteration
+// expands at least one state, so the log size bounds it) was reached.
+__global__ void guided_advance_kernel(const GuidedArgs a) {
+  GuidedCtl& c = *a.ctl;
+  c.iters += 1;
+  const bool more = c.found == ~0ull && !c.done && !c.error && c.iters < a.max_iters;
+  cudaGraphSetConditional(a.cond, more ? 1u : 0u);
+}
+
+// One thread: follow the parent log indices from the deadlock back to the
+// initial state, writing the path (deadlock first, E words per state) to out;
+// c.path_len = its length, or 0 when it does not fit in cap states.
+template <int W>
+__global__ void guided_path_kernel(const GuidedArgs a, uint32_t* out, uint64_t cap) {
+  constexpr int E = W + 1;
+  GuidedCtl& c = *a.ctl;
+  c.path_len = 0;
+  if (c.found == ~0ull) return;
+  uint64_t li = c.found, n = 0;
+  while (n < cap) {
+    const uint32_t* e = a.log + li * E;
+#pragma unroll
+    for (int w = 0; w < E; ++w) out[n * E + w] = e[w];
+    ++n;
+    if (e[W] == 0xFFFFFFFFu) {
+      c.path_len = n;
+      return;
+    }
+    li = e[W];
+  }
+}
+
 }  // namespace gxd
 
 namespace gx {
@@ -462,6 +508,7 @@ struct GKernels {
   const void* select;
   const void* expand;
   const void* score;
+  const void* path;
 };
 
 template <int W, int B>
@@ -469,7 +516,8 @@ GKernels gk() {
   return GKernels{&gxd::label_sweep_kernel<W, B>, reinterpret_cast<const void*>(&gxd::guided_init_kernel<W, B>),
                   reinterpret_cast<const void*>(&gxd::guided_select_kernel<W>),
                   reinterpret_cast<const void*>(&gxd::guided_expand_kernel<W, B>),
-                  reinterpret_cast<const void*>(&gxd::guided_score_kernel<W>)};
+                  reinterpret_cast<const void*>(&gxd::guided_score_kernel<W>),
+                  reinterpret_cast<const void*>(&gxd::guided_path_kernel<W>)};
 }
 
 bool gk_lookup(int W, int B, GKernels& k) {
@@ -547,6 +595,82 @@ gx_status guided_plan(const Net& net, const gx_explore_opts* o, GPlan& P) {
 
 }  // namespace
 
+void release_guided(gx_net* h) {
+  if (h->guided_exec) cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(h->guided_exec));
+  if (h->guided_graph) cudaGraphDestroy(static_cast<cudaGraph_t>(h->guided_graph));
+  h->guided_exec = nullptr;
+  h->guided_graph = nullptr;
+  h->guided_key.clear();
+}
+
+namespace {
+
+// One guided search as a graph: clear the control block, bins and table,
+// insert the initial state, then WHILE(cond) {select, expand, score, advance}.
+gx_status build_guided_graph(gx_net* h, const GPlan& P, GuidedArgs a, int grid, size_t smem, int score_grid) {
+  release_guided(h);
+  h->release_guided = &release_guided;
+  cudaGraph_t g;
+  GG_CUDA(cudaGraphCreate(&g, 0));
+  h->guided_graph = g;
+  cudaGraphConditionalHandle cond;
+  GG_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+  a.cond = cond;
+  std::vector<cudaGraphNode_t> clears;
+  auto add_memset = [&](void* dst, uint64_t words) -> cudaError_t {
+    cudaMemsetParams mp{};
+    mp.dst = dst;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = words;
+    mp.height = 1;
+    cudaGraphNode_t nd;
+    cudaError_t e = cudaGraphAddMemsetNode(&nd, g, nullptr, 0, &mp);
+    clears.push_back(nd);
+    return e;
+  };
+  GG_CUDA(add_memset(a.ctl, sizeof(GuidedCtl) / 4));
+  GG_CUDA(add_memset(a.bin_count, 2ull * P.nbins));
+  const uint64_t words = (uint64_t)P.B * P.nb;
+  constexpr uint64_t kPiece = 1ull << 30;
+  for (uint64_t w0 = 0; w0 < words; w0 += kPiece) GG_CUDA(add_memset(a.table + w0, std::min(kPiece, words - w0)));
+  auto add_kernel = [&](cudaGraph_t gr, const cudaGraphNode_t* deps, size_t nd, const void* fn, dim3 gd, dim3 bd,
+                        size_t sh, cudaGraphNode_t* out) -> cudaError_t {
+    void* args[] = {&a};
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(fn);
+    kp.gridDim = gd;
+    kp.blockDim = bd;
+    kp.sharedMemBytes = (unsigned)sh;
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, gr, deps, nd, &kp);
+  };
+  cudaGraphNode_t reset, init, start, sel, ex, sc, adv, cnode;
+  GG_CUDA(add_kernel(g, clears.data(), clears.size(), reinterpret_cast<const void*>(&gxd::guided_reset_kernel),
+                     dim3(1), dim3(1), 0, &reset));
+  GG_CUDA(add_kernel(g, &reset, 1, P.k.init, dim3(1), dim3(32), 0, &init));
+  GG_CUDA(add_kernel(g, &init, 1, reinterpret_cast<const void*>(&gxd::guided_loop_start_kernel), dim3(1), dim3(1), 0,
+                     &start));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  GG_CUDA(cudaGraphAddNode(&cnode, g, &start, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  GG_CUDA(add_kernel(body, nullptr, 0, P.k.select, dim3(1), dim3(1024), 0, &sel));
+  GG_CUDA(add_kernel(body, &sel, 1, P.k.expand, dim3(grid), dim3(kBlock), smem, &ex));
+  GG_CUDA(add_kernel(body, &ex, 1, P.k.score, dim3(score_grid), dim3(gxt::kRows), gxt::kTcSmemBytes, &sc));
+  GG_CUDA(add_kernel(body, &sc, 1, reinterpret_cast<const void*>(&gxd::guided_advance_kernel), dim3(1), dim3(1), 0,
+                     &adv));
+  cudaGraphExec_t exec;
+  GG_CUDA(cudaGraphInstantiate(&exec, g, 0));
+  h->guided_exec = exec;
+  return GX_OK;
+}
+
+}  // namespace
+
 gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t ws_bytes, cudaStream_t st) {
   const Net& net = h->net;
   if (!h->guided_params) return fail(GX_ERR_INVALID, "guided mode needs scoring weights (gx_guided_set_weights)");
@@ -604,24 +728,49 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
   GG_CUDA(cudaEventCreate(&e1));
   GG_CUDA(cudaEventRecord(e0, st));
   GG_CUDA(cudaMemcpyAsync(base + P.off_blob, net.blob.data(), blob_bytes, cudaMemcpyHostToDevice, st));
-  GuidedCtl init{};
-  init.found = ~0ull;
-  GG_CUDA(cudaMemcpyAsync(ctl, &init, sizeof(init), cudaMemcpyHostToDevice, st));
-  GG_CUDA(cudaMemsetAsync(a.bin_count, 0, 8ull * P.nbins, st));
-  GG_CUDA(cudaMemsetAsync(a.table, 0, 4ull * P.B * P.nb, st));
-  void* args[] = {&a};
-  GG_CUDA(cudaLaunchKernel(P.k.init, dim3(1), dim3(32), args, 0, st));
+  a.max_iters = P.log_cap + 2;  // each iteration expands a state or ends the search
   GuidedCtl hc{};
   uint64_t iters = 0;
-  while (true) {
-    GG_CUDA(cudaLaunchKernel(P.k.select, dim3(1), dim3(1024), args, 0, st));
-    GG_CUDA(cudaLaunchKernel(P.k.expand, dim3(grid), dim3(kBlock), args, smem, st));
-    GG_CUDA(cudaLaunchKernel(P.k.score, dim3(score_grid), dim3(gxt::kRows), args, gxt::kTcSmemBytes, st));
-    GG_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    GG_CUDA(cudaStreamSynchronize(st));
-    ++iters;
-    if (hc.found != ~0ull || hc.done || hc.error) break;
+  const bool device_loop = !(opts && opts->host_loop);
+  if (device_loop) {
+    // the graph holds the arguments by value: rebuild it when anything changes
+    std::vector<unsigned char> key(sizeof(gx_explore_opts) + 4 * sizeof(uint64_t));
+    const uint64_t extra[4] = {reinterpret_cast<uint64_t>(ws), P.total, reinterpret_cast<uint64_t>(a.params),
+                               (uint64_t)smem};
+    if (opts) std::memcpy(key.data(), opts, sizeof(gx_explore_opts));
+    std::memcpy(key.data() + sizeof(gx_explore_opts), extra, sizeof(extra));
+    if (!h->guided_exec || h->guided_key != key) {
+      s = build_guided_graph(h, P, a, grid, smem, score_grid);
+      if (s != GX_OK) return s;
+      h->guided_key = key;
+    }
+    GG_CUDA(cudaGraphLaunch(static_cast<cudaGraphExec_t>(h->guided_exec), st));
+  } else {
+    GuidedCtl init{};
+    init.found = ~0ull;
+    GG_CUDA(cudaMemcpyAsync(ctl, &init, sizeof(init), cudaMemcpyHostToDevice, st));
+    GG_CUDA(cudaMemsetAsync(a.bin_count, 0, 8ull * P.nbins, st));
+    GG_CUDA(cudaMemsetAsync(a.table, 0, 4ull * P.B * P.nb, st));
+    void* args[] = {&a};
+    GG_CUDA(cudaLaunchKernel(P.k.init, dim3(1), dim3(32), args, 0, st));
+    while (true) {
+      GG_CUDA(cudaLaunchKernel(P.k.select, dim3(1), dim3(1024), args, 0, st));
+      GG_CUDA(cudaLaunchKernel(P.k.expand, dim3(grid), dim3(kBlock), args, smem, st));
+      GG_CUDA(cudaLaunchKernel(P.k.score, dim3(score_grid), dim3(gxt::kRows), args, gxt::kTcSmemBytes, st));
+      GG_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
+      GG_CUDA(cudaStreamSynchronize(st));
+      ++iters;
+      if (hc.found != ~0ull || hc.done || hc.error) break;
+    }
   }
+  // the deadlock's path, walked on the device into the batch buffer (free now)
+  {
+    uint32_t* out = a.batch;
+    uint64_t cap = a.batch_cap;
+    void* pargs[] = {&a, &out, &cap};
+    GG_CUDA(cudaLaunchKernel(P.k.path, dim3(1), dim3(1), pargs, 0, st));
+  }
+  GG_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
   GG_CUDA(cudaEventRecord(e1, st));
   GG_CUDA(cudaStreamSynchronize(st));
   float ms = 0;
@@ -634,7 +783,20 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
   h->deadlocks.clear();
   h->violations.clear();
   const int E = P.W + 1;
-  if (hc.found != ~0ull) {
+  if (device_loop) iters = hc.iters;
+  if (hc.found != ~0ull && hc.path_len > 0) {
+    // deadlock first in the buffer: reverse while unpacking
+    std::vector<uint32_t> raw(hc.path_len * (uint64_t)E);
+    GG_CUDA(cudaMemcpy(raw.data(), a.batch, 4ull * raw.size(), cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> local(net.n_procs);
+    for (uint64_t i = hc.path_len; i-- > 0;) {
+      uint32_t w4[4] = {0, 0, 0, 0};
+      for (int w = 0; w < P.W; ++w) w4[w] = raw[i * E + w];
+      unpack_host(net, w4, local.data());
+      h->guided_trace.insert(h->guided_trace.end(), local.begin(), local.end());
+    }
+    h->deadlocks = local;
+  } else if (hc.found != ~0ull) {  // a path longer than the batch buffer: one entry at a time
     std::vector<std::vector<uint32_t>> path;
     uint64_t li = hc.found;
     while (true) {

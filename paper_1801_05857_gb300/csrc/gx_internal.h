@@ -78,11 +78,17 @@ struct gx_net {
   void* loop_exec = nullptr;
   std::vector<unsigned char> loop_key;
   void (*release)(gx_net*) = nullptr;
+  // the same for the guided search's iteration loop
+  void* guided_graph = nullptr;
+  void* guided_exec = nullptr;
+  std::vector<unsigned char> guided_key;
+  void (*release_guided)(gx_net*) = nullptr;
   gx_net() = default;
   gx_net(const gx_net&) = delete;
   gx_net& operator=(const gx_net&) = delete;
   ~gx_net() {
     if (release) release(this);
+    if (release_guided) release_guided(this);
   }
 };
 

@@ -161,3 +161,33 @@ def test_guided_search_without_deadlock_is_exhaustive(cuda):
     r = oracle.explore(net)
     assert s["states"] == r.states and s["explored"] == r.states
     assert s["transitions"] == r.transitions
+
+
+@pytest.mark.parametrize("host_loop", [0, 1])
+def test_device_and_host_iteration_loops(cuda, host_loop):
+    """The guided search runs as one graph (device loop) or one host round trip
+    per iteration; both find a replayable deadlock, and both are exhaustive on a
+    network without one."""
+    params, _ = _trained(200)
+    net = inputs.planted_network(10, 9, n_traps=1)
+    h, n, found, s = _guided(net, params, host_loop=host_loop)
+    assert n == 1 and s["deadlock_count"] == 1
+    trace = gx.guided_trace(h)
+    _replay(net, trace)
+    assert list(found[0]) == list(trace[-1])
+    ring = inputs.token_ring(7)
+    _, n2, _, s2 = _guided(ring, params, host_loop=host_loop, guided_batch=512)
+    r = oracle.explore(ring)
+    assert n2 == 0 and s2["complete"] == 1 and (s2["states"], s2["transitions"]) == (r.states, r.transitions)
+
+
+def test_path_longer_than_the_batch_buffer(cuda):
+    """With 16-state batches the deadlock's path (2n + 1 states deep) no longer fits
+    the buffer the device walk uses, and the host walks it entry by entry."""
+    params, _ = _trained(200)
+    net = inputs.planted_network(3, 10, n_traps=1)
+    h, n, found, s = _guided(net, params, guided_batch=16)
+    assert n == 1
+    trace = gx.guided_trace(h)
+    assert len(trace) > 16
+    _replay(net, trace)
