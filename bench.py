@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--table-log2-words", type=int, default=28)
     ap.add_argument("--slice-log2", type=int, default=0)
     ap.add_argument("--nodes", type=int, default=19, help="token-ring nodes for --experiment scaled")
+    ap.add_argument("--family", default="ring", choices=["ring", "product"],
+                    help="--experiment scaled: token ring (--nodes) or the memory-scaled product network")
     ap.add_argument("--warp-cache", type=int, default=9,
                     help="log2 entries of the per-warp cache of seen vectors (0 = off)")
     ap.add_argument("--level-loop", default="host", choices=["host", "device"],
@@ -362,19 +364,27 @@ def guided_part(torch, gx, inputs, guide) -> dict:
         per = []
         for seed in range(5):
             net = inputs.planted_network(seed, n, n_traps=k)
-            per.append({"network": net.name, "guided": guided(net, params), "untrained": guided(net, untrained),
+            # the guided search is not deterministic (concurrent pushes order the bins):
+            # five runs per seed; the untrained guide and BFS once
+            runs = [guided(net, params) for _ in range(5)]
+            per.append({"network": net.name, "guided_runs": runs, "untrained": guided(net, untrained),
                         "bfs": bfs(net) if n <= 14 else {"skipped": "table beyond 24 GiB"}})
         rows.extend(per)
 
-        def med(arm, key):
-            v = sorted(r[arm][key] for r in per if r[arm].get("found"))
+        def med(vals):
+            v = sorted(vals)
             return v[len(v) // 2] if v else None
 
-        summary.append({"processes": n, "planted_deadlocks": k, "seeds": 5,
-                        **{f"{arm}_found": sum(1 for r in per if r[arm].get("found")) for arm in
-                           ("guided", "untrained", "bfs")},
-                        **{f"{arm}_median_{key}": med(arm, key) for arm in ("guided", "untrained", "bfs")
-                           for key in ("explored", "ms")}})
+        g_runs = [x for r in per for x in r["guided_runs"] if x.get("found")]
+        summary.append({"processes": n, "planted_deadlocks": k, "seeds": 5, "guided_runs_per_seed": 5,
+                        "guided_found": len(g_runs),
+                        "guided_median_explored": med([x["explored"] for x in g_runs]),
+                        "guided_median_ms": med([x["ms"] for x in g_runs]),
+                        "guided_ms_range": [min(x["ms"] for x in g_runs), max(x["ms"] for x in g_runs)]
+                        if g_runs else None,
+                        **{f"{arm}_found": sum(1 for r in per if r[arm].get("found")) for arm in ("untrained", "bfs")},
+                        **{f"{arm}_median_{key}": med([r[arm][key] for r in per if r[arm].get("found")])
+                           for arm in ("untrained", "bfs") for key in ("explored", "ms")}})
     lo = losses.cpu().numpy()
     return {"train": {"networks": len(train_nets), "examples": int(hist.shape[0]),
                       "label_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3), "steps": 1500,
@@ -626,12 +636,48 @@ def run_ours(args, world, rank, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def product_closed_form(net, blocks):
+    """States and transitions of inputs.product_network (its reachable set is the
+    product of the blocks): every local edge fires in every combination of the other
+    processes' block states, every rule once per combination of its participants'
+    matching edges and of the others' block states."""
+    S = 1
+    for c in blocks:
+        S *= c
+    in_rule = [set() for _ in net.procs]
+    for r in net.rules:
+        for p, a in r.parts:
+            in_rule[p].add(a)
+    T = 0
+    for p, lts in enumerate(net.procs):
+        T += sum(1 for s, a, t in lts.edges if s < blocks[p] and a not in in_rule[p]) * (S // blocks[p])
+    for r in net.rules:
+        m, c = 1, 1
+        for p, a in r.parts:
+            m *= sum(1 for s, b, t in net.procs[p].edges if s < blocks[p] and b == a)
+            c *= blocks[p]
+        T += m * (S // c)
+    return S, T
+
+
+# the memory-scaled product network: 20 processes x 16 local states (4-word slots),
+# 3-party rules on 10 % of 30 labels, reachable blocks 3^18 * 4 * 5 = 7.75e9 states
+PRODUCT_SCALED = dict(seed=7, n_procs=20, n_states=16, blocks=[3] * 18 + [4, 5])
+
+
 def scaled_experiment(torch, gx, inputs, args):
-    """Memory-scaled exploration: the token ring with --nodes nodes (2N 3^(N-1) states,
-    4 N^2 3^(N-2) transitions) in a table of 2^--table-log2-words words; one line per
-    level with the table fill after it, then a summary binned by fill."""
+    """Memory-scaled exploration in a table of 2^--table-log2-words words; one line per
+    level with the table fill after it, then a summary binned by fill.  --family ring:
+    the token ring with --nodes nodes (2N 3^(N-1) states, 4 N^2 3^(N-2) transitions);
+    --family product: inputs.product_network(**PRODUCT_SCALED) (closed forms above)."""
     n = args.nodes
-    net = inputs.token_ring(n)
+    if args.family == "product":
+        net = inputs.product_network(**PRODUCT_SCALED)
+        want_states, want_trans = product_closed_form(net, PRODUCT_SCALED["blocks"])
+    else:
+        net = inputs.token_ring(n)
+        want_states = 2 * n * 3 ** (n - 1)
+        want_trans = 4 * n * n * 3 ** (n - 2)
     h = gx.load_network(net)
     o = gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
                         table_bytes=4 << args.table_log2_words, slice_log2=args.slice_log2,
@@ -641,8 +687,6 @@ def scaled_experiment(torch, gx, inputs, args):
     s = gx.stats(h)
     lv = gx.levels(h)
     prof = gx.level_profile(h)
-    want_states = 2 * n * 3 ** (n - 1)
-    want_trans = 4 * n * n * 3 ** (n - 2)
     W = s["slot_words"]
     bucket_bytes = max(32, 4 * s["bucket_words"])
     found = 1

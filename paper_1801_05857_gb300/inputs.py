@@ -233,6 +233,61 @@ def random_network(seed: int, n_procs: int, n_states, deg_lo: int = 1, deg_hi: i
     return Network(n_labels, procs, rules, name=name or f"random_s{seed}_n{n_procs}")
 
 
+def product_network(seed: int, n_procs: int, n_states: int, blocks, n_labels: int = 30,
+                    sync_frac: float = 0.1, parties: int = 3, deg_lo: int = 1, deg_hi: int = 3,
+                    name: str = "") -> Network:
+    """Memory-scaled family whose reachable set is a product (counts in closed form).
+
+    * blocks: int or one entry per process: process p reaches local states
+      0..blocks[p]-1 (its block) and no other; the remaining states up to
+      n_states exist only to widen the vector (bits = ceil(log2 n_states)).
+    * round(sync_frac * n_labels) labels synchronise, each as one rule over
+      `parties` distinct processes; the other labels are local.
+    * Every block state has a local edge to the next block state (a cycle, so
+      the block is reachable and no state is a deadlock) plus
+      U{deg_lo-1..deg_hi-1} more edges inside the block, labelled with a local
+      label or one of the process's rule labels.  States outside the block
+      only have edges among themselves.
+    Every combination of block states is then reachable by local moves, and
+    rule edges never leave the blocks, so the state space is the product of
+    the blocks.
+    """
+    sizes = list(blocks) if isinstance(blocks, (list, tuple)) else [blocks] * n_procs
+    assert all(1 <= c <= n_states for c in sizes)
+    top = substream(seed, 0)
+    n_sync = max(1, int(round(sync_frac * n_labels)))
+    rules, member = [], [[] for _ in range(n_procs)]
+    for a in range(n_sync):
+        ps = sorted(top.sample(n_procs, parties))
+        rules.append(Rule([(p, a) for p in ps], a))
+        for p in ps:
+            member[p].append(a)
+    local = list(range(n_sync, n_labels))
+    procs = []
+    for p in range(n_procs):
+        rng = substream(seed, 4, p)
+        c = sizes[p]
+        pool = local + member[p]
+        edges = []
+        for lo, hi in ((0, c), (c, n_states)):
+            for st in range(lo, hi):
+                seen = set()
+                if lo == 0:  # the block's cycle
+                    a = local[rng.below(len(local))]
+                    t = lo + (st - lo + 1) % (hi - lo)
+                    seen.add((a, t))
+                    edges.append((st, a, t))
+                extra = rng.between(deg_lo, deg_hi) - (1 if lo == 0 else 0)
+                while len(seen) < extra + (1 if lo == 0 else 0):
+                    a = pool[rng.below(len(pool))]
+                    t = lo + rng.below(hi - lo)
+                    if (a, t) not in seen:
+                        seen.add((a, t))
+                        edges.append((st, a, t))
+        procs.append(LTS(n_states, 0, edges))
+    return Network(n_labels, procs, rules, name=name or f"product_s{seed}_n{n_procs}")
+
+
 def planted_network(seed: int, n_procs: int, n_traps: int = 1, n_states: int = 16,
                     deg_lo: int = 1, deg_hi: int = 3, cluster: int = 3, sync_frac: float = 0.3,
                     risk_edges: int = 2, name: str = "") -> Network:

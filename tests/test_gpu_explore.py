@@ -320,3 +320,26 @@ def test_device_loop_max_levels_and_repeated_graph_launches(cuda):
     for _ in range(3):
         gx.explore(h, o, ws)
         assert gx.stats(h)["states"] == r.states
+
+
+def _product_closed_form(net, blocks):
+    from test_oracle import product_closed_form
+    return product_closed_form(net, blocks)
+
+
+@pytest.mark.parametrize("seed,n,ns,blocks", [
+    (0, 8, 16, [2, 3, 2, 3, 2, 2, 3, 2]),              # 1 word
+    (1, 16, 16, [2] * 12 + [3] * 4),                   # 3 words -> 4-word slots, 3.3e5 states
+    (2, 20, 16, [2] * 16 + [3, 3, 4, 4]),              # 4-word slots, 9.4e6 states
+    (3, 16, 64, [3] * 10 + [2] * 6)])                  # 6 bits a process, 4-word slots, 3.8e6 states
+def test_product_family_against_closed_forms(cuda, seed, n, ns, blocks):
+    """The memory-scaled family (3-party rules on 10 % of the labels): states and
+    transitions equal the closed forms pinned on the oracle; the first
+    instance is also checked level by level against the oracle."""
+    net = inputs.product_network(seed, n, ns, blocks)
+    S, T = _product_closed_form(net, blocks)
+    if S < 10 ** 5:
+        s = assert_parity(net, table_bytes=1 << 24)
+    else:
+        _, s, _, _ = run_gpu(net, table_bytes=1 << 30, bucket_words=32, hash_rounds=32)
+    assert (s["states"], s["transitions"], s["deadlock_count"], s["complete"]) == (S, T, 0, 1)

@@ -389,3 +389,38 @@ def test_producer_consumers_family_closed_forms(k):
     assert r.deadlock_count == 0
     if k == 2:
         assert (r.states, r.transitions) == (8, 24)
+
+
+def product_closed_form(net, blocks):
+    """States and transitions of inputs.product_network: the reachable set is the
+    product of the blocks, so a process's local edge fires in every combination
+    of the others' block states, and a rule fires once per combination of its
+    participants' matching edges times every combination of the rest."""
+    S = int(np.prod(blocks))
+    in_rule = [set() for _ in net.procs]
+    for r in net.rules:
+        for p, a in r.parts:
+            in_rule[p].add(a)
+    T = 0
+    for p, lts in enumerate(net.procs):
+        local = sum(1 for s, a, t in lts.edges if s < blocks[p] and a not in in_rule[p])
+        T += local * (S // blocks[p])
+    for r in net.rules:
+        m, c = 1, 1
+        for p, a in r.parts:
+            m *= sum(1 for s, b, t in net.procs[p].edges if s < blocks[p] and b == a)
+            c *= blocks[p]
+        T += m * (S // c)
+    return S, T
+
+
+@pytest.mark.parametrize("seed,n,ns,blocks,parties", [
+    (0, 6, 8, [2, 3, 2, 3, 2, 2], 3), (1, 8, 16, [2, 3, 2, 3, 2, 2, 3, 2], 3),
+    (2, 7, 16, [4, 1, 3, 2, 2, 3, 2], 2), (3, 9, 6, 2, 3), (4, 5, 64, [5, 4, 3, 6, 2], 3)])
+def test_product_family_closed_forms(seed, n, ns, blocks, parties):
+    net = inputs.product_network(seed, n, ns, blocks, parties=parties)
+    b = blocks if isinstance(blocks, list) else [blocks] * n
+    S, T = product_closed_form(net, b)
+    r = oracle.explore(net)
+    assert (r.states, r.transitions, r.deadlock_count) == (S, T, 0)
+    assert any(len(rule.parts) == parties for rule in net.rules)
