@@ -174,26 +174,62 @@ __global__ void __launch_bounds__(1024) batch_advance_kernel(const BatchArgs a, 
 // chunk of another network.
 constexpr int kBatchCacheLog2 = 9;
 
+// The network a warp is working on, staged in shared memory when the warp
+// moves to it, so that its layout and table pointers take no registers in the
+// inner loop.
+struct WarpNet {
+  NetBlobLayout lay;
+  const uint32_t* blob;
+  uint32_t* table;
+  unsigned long long* next_end;
+  uint32_t* frontier;
+  uint64_t fmask, cur_begin;
+  int log2nb;
+};
+
+struct SmemTarget {
+  const WarpNet* w;
+  int nrounds;
+  __device__ __forceinline__ uint32_t* table() const { return w->table; }
+  __device__ __forceinline__ int log2nb() const { return w->log2nb; }
+  __device__ __forceinline__ int rounds() const { return nrounds; }
+  __device__ __forceinline__ unsigned long long* next_end() const { return w->next_end; }
+  __device__ __forceinline__ uint32_t* frontier() const { return w->frontier; }
+  __device__ __forceinline__ uint64_t fmask() const { return w->fmask; }
+  __device__ __forceinline__ uint64_t begin() const { return w->cur_begin; }
+};
+
+// The batched kernel keeps a network index and chunk bounds besides the
+// single-network kernel's state: one CTA per SM fewer (at most 4) keeps its
+// common instantiations free of spills; 4 and 5 measured the same time.
 template <int W, int B, int G>
-__global__ void __launch_bounds__(gx::kBlock) batch_expand_kernel(const BatchArgs a) {
+struct BatchOcc {
+  static constexpr int min_ctas = ExpandOcc<W, B, G>::min_ctas < 4 ? ExpandOcc<W, B, G>::min_ctas : 4;
+};
+
+template <int W, int B, int G>
+__global__ void __launch_bounds__(gx::kBlock, BatchOcc<W, B, G>::min_ctas) batch_expand_kernel(const BatchArgs a) {
   __shared__ uint64_t muls[kMaxRounds];
   for (int i = threadIdx.x; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
   constexpr int CW = W <= 2 ? W : 1;
   __shared__ __align__(16) uint32_t cache_mem[gx::kBlock / 32][(1 << kBatchCacheLog2) * CW];
+  __shared__ WarpNet s_net[gx::kBlock / 32];
   __syncthreads();
+  WarpNet& wn = s_net[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
   const Group<G> g;
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
   WarpCache cache{W <= 2 ? cache_mem[threadIdx.x >> 5] : nullptr, (1u << kBatchCacheLog2) - 1u};
   int cached_net = -1;
-  const unsigned long long total = a.prefix[a.n];
+  __shared__ unsigned long long s_chunk[gx::kBlock / 32][2];  // [first, end) of the warp's chunk
+  unsigned long long* chunk_range = s_chunk[threadIdx.x >> 5];
   constexpr int K = PerLane<G>::K;
   while (true) {
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(a.claim, 1ull);
     c = __shfl_sync(FULLMASK, c, 0);
-    if (c >= total) break;
+    if (c >= __ldcg(a.prefix + a.n)) break;  // chunks of this iteration, all networks
     // the network whose chunks contain c: largest i with prefix[i] <= c
     int lo = 0, hi = a.n - 1;
     while (lo < hi) {
@@ -202,25 +238,41 @@ __global__ void __launch_bounds__(gx::kBlock) batch_expand_kernel(const BatchArg
       else hi = mid - 1;
     }
     BNet& b = a.nets[lo];
-    if (W <= 2 && lo != cached_net) {  // the cache holds one network's vectors at a time
-      for (uint32_t i = lane; i < (1u << kBatchCacheLog2) * CW; i += 32) cache_mem[threadIdx.x >> 5][i] = 0u;
+    if (lo != cached_net) {  // stage the network; the cache holds one network's vectors at a time
+      if (lane == 0) {
+        wn.lay = b.lay;
+        wn.blob = b.blob;
+        wn.table = b.table;
+        wn.next_end = &b.next_end;
+        wn.frontier = b.frontier;
+        wn.fmask = b.fmask;
+        wn.cur_begin = b.cur_begin;
+        wn.log2nb = b.log2nb;
+      }
+      if (W <= 2)
+        for (uint32_t i = lane; i < (1u << kBatchCacheLog2) * CW; i += 32) cache_mem[threadIdx.x >> 5][i] = 0u;
       __syncwarp();
       cached_net = lo;
     }
-    const uint32_t* t = b.blob;
-    const NetBlobLayout L = b.lay;
-    const Target tg{b.table, b.log2nb, a.rounds, &b.next_end, b.frontier, b.fmask, b.cur_begin};  // per network
-    const uint64_t first = b.cur_begin + (c - __ldcg(a.prefix + lo)) * (uint64_t)a.chunk;
-    const uint64_t end = b.cur_end;
-    unsigned long long trans = 0;
+    const uint32_t* t = wn.blob;
+    const NetBlobLayout& L = wn.lay;
+    const SmemTarget tg{&wn, a.rounds};
+    if (lane == 0) {
+      const uint64_t first = wn.cur_begin + (c - __ldcg(a.prefix + lo)) * (uint64_t)a.chunk;
+      const uint64_t end = b.cur_end;
+      chunk_range[0] = first;
+      chunk_range[1] = first + a.chunk < end ? first + a.chunk : end;
+    }
+    __syncwarp();
+    uint32_t trans = 0;  // per chunk: far below 2^32
     uint32_t probes = 0, err = 0;
-    for (uint64_t sub = first; sub < first + a.chunk && sub < end; sub += 32) {
+    for (uint64_t sub = chunk_range[0]; sub < chunk_range[1]; sub += 32) {
       const uint64_t idx = sub + lane;
-      const bool valid = idx < end && idx < first + a.chunk;
+      const bool valid = idx < chunk_range[1];
       uint32_t v[W];
 #pragma unroll
       for (int w = 0; w < W; ++w) v[w] = 0;
-      if (valid) load_vec<W>(b.frontier + (idx & b.fmask) * W, v);
+      if (valid) load_vec<W>(wn.frontier + (idx & wn.fmask) * W, v);
       uint32_t remaining = valid ? count_succ<W>(t, L, v) : 0u;
       trans += remaining;
       if (valid && remaining == 0) {
@@ -249,11 +301,11 @@ __global__ void __launch_bounds__(gx::kBlock) batch_expand_kernel(const BatchArg
       }
     }
     st.flush<W>(tg, err);
-    trans = warp_sum(trans);
+    const unsigned long long tr = warp_sum((unsigned long long)trans);
     const unsigned long long pr = warp_sum((unsigned long long)probes);
     err = __reduce_or_sync(FULLMASK, err);
     if (lane == 0) {
-      if (trans) atomicAdd(&b.transitions, trans);
+      if (tr) atomicAdd(&b.transitions, tr);
       if (pr) atomicAdd(&b.probes, pr);
       if (err) atomicOr(&b.error, err);
     }
