@@ -21,6 +21,9 @@
  *     stream).  Device work is issued on it; calls that return host-visible
  *     results synchronise that stream before returning.
  *   - Input arrays are owned by the caller and are only read during the call.
+ *   - Threads: calls on different gx_net / gx_batch handles may run
+ *     concurrently; calls on the same handle must not (a handle keeps the
+ *     last search's results and its cached CUDA graphs).
  */
 #ifndef GX_H
 #define GX_H

@@ -207,9 +207,9 @@ namespace {
       return gx::fail(GX_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
   } while (0)
 
+// Kernel attributes belong to the current device, so they are set on every
+// call (a few microseconds) rather than once per process.
 gx_status set_smem() {
-  static bool done = false;
-  if (done) return GX_OK;
   GM_CUDA(cudaFuncSetAttribute(gxm::grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)gxm::kGradSmemBytes));
   GM_CUDA(cudaFuncSetAttribute(gxm::mlp_tc_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -217,7 +217,6 @@ gx_status set_smem() {
   // all of the SM's unified L1/shared memory as shared memory, so that 3 tiles fit per SM
   GM_CUDA(cudaFuncSetAttribute(gxm::mlp_tc_forward_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                (int)cudaSharedmemCarveoutMaxShared));
-  done = true;
   return GX_OK;
 }
 }  // namespace
