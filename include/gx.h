@@ -309,8 +309,13 @@ gx_status gx_set_digest(gx_net* net, void* workspace, uint64_t workspace_bytes, 
 #define GX_MLP_HIDDEN 128
 #define GX_MLP_PARAMS (GX_MLP_HIDDEN * GX_MLP_IN + GX_MLP_HIDDEN + GX_MLP_HIDDEN * GX_MLP_HIDDEN + \
                        GX_MLP_HIDDEN + GX_MLP_HIDDEN + 1)
-/* Device bytes of the optimiser state gx_mlp_train needs for a batch size. */
-#define GX_MLP_STATE_BYTES(batch) (4ull * (3ull * GX_MLP_PARAMS + 2ull) + 8ull * (batch))
+/* CTAs of the gradient kernel at most; each writes its own partial gradient,
+ * which a second kernel sums in a fixed order (gradients are deterministic). */
+#define GX_MLP_GRAD_CTAS 256
+/* Device bytes of the optimiser state gx_mlp_train needs for a batch size:
+ * Adam moments, the gradient, the partial gradients and the batch indices. */
+#define GX_MLP_STATE_BYTES(batch) \
+  (4ull * ((3ull + GX_MLP_GRAD_CTAS) * GX_MLP_PARAMS + GX_MLP_GRAD_CTAS + 2ull) + 8ull * (batch))
 
 /* Training examples from the last gx_explore on `net` (same workspace): every
  * state found gets its distance to the nearest deadlock (backward
@@ -335,7 +340,9 @@ gx_status gx_mlp_init(float* params, uint64_t seed, void* stream);
 gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, float* out, void* stream);
 
 /* Gradient of the mean squared error over n examples at params (grad: device,
- * GX_MLP_PARAMS floats; loss: device, one float). */
+ * GX_MLP_PARAMS floats, overwritten; loss: device, one float).  The result
+ * does not depend on scheduling (partial gradients summed in a fixed order);
+ * scratch for them is allocated on `stream` and freed before returning. */
 gx_status gx_mlp_grad(const float* params, const uint8_t* hist, const float* label, uint64_t n,
                       float* grad, float* loss, void* stream);
 

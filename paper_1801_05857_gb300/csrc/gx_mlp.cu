@@ -47,7 +47,8 @@ constexpr int OFF_B3 = OFF_W3 + H;
 constexpr int NPARAM = OFF_B3 + 1;
 static_assert(NPARAM == GX_MLP_PARAMS, "parameter count");
 constexpr int LD2 = H + 1;  // padded row of W2 in shared memory (no bank conflicts)
-constexpr int EPB = 16;     // examples per CTA in the training kernel
+constexpr int EPB = 16;     // examples per chunk of the gradient kernel
+constexpr int kGradCtas = GX_MLP_GRAD_CTAS;  // at most this many CTAs, one partial gradient each
 
 __device__ __forceinline__ float bf(float w) { return __bfloat162float(__float2bfloat16_rn(w)); }
 
@@ -62,13 +63,15 @@ __device__ __forceinline__ float block_sum128(float v, float* red) {
   return t;
 }
 
-// Forward and backward of EPB examples per CTA on the CUDA cores; thread k
-// owns hidden unit k.  Gradients of the mean loss over n examples are added
-// to g, and the mean loss to *loss.
+// Forward and backward on the CUDA cores; thread k owns hidden unit k.  CTA
+// c takes the chunks of EPB examples c, c + gridDim.x, ... and writes its
+// part of the gradient of the mean loss over n examples to partial[c] (and
+// its part of the loss to partial_loss[c]); reduce_kernel sums the parts in a
+// fixed order, so a gradient does not depend on the order CTAs finish in.
 __global__ void __launch_bounds__(H) grad_kernel(const float* __restrict__ p, const uint8_t* __restrict__ hist,
                                                  const float* __restrict__ label, uint64_t n,
                                                  const uint64_t* __restrict__ index, float inv_n,
-                                                 float* __restrict__ g, float* __restrict__ loss) {
+                                                 float* __restrict__ partial, float* __restrict__ partial_loss) {
   extern __shared__ float sm[];
   float* W2 = sm;                 // [H][LD2]
   float* gW2 = W2 + H * LD2;      // [H][LD2]
@@ -90,8 +93,10 @@ __global__ void __launch_bounds__(H) grad_kernel(const float* __restrict__ p, co
   for (int i = 0; i < IN; ++i) gw1[i] = 0.f;
   float gb1 = 0.f, gb2 = 0.f, gw3 = 0.f, gb3 = 0.f, lsum = 0.f;
   __syncthreads();
+  const uint64_t chunks = (n + EPB - 1) / EPB;
+  for (uint64_t chunk = blockIdx.x; chunk < chunks; chunk += gridDim.x)
   for (int e = 0; e < EPB; ++e) {
-    const uint64_t slot = (uint64_t)blockIdx.x * EPB + e;
+    const uint64_t slot = chunk * EPB + e;
     if (slot >= n) break;  // uniform in the block
     const uint64_t ex = index ? index[slot] : slot;
     if (k < 32) {  // warp 0: x = bf16(hist * (1 / number of processes))
@@ -130,15 +135,32 @@ __global__ void __launch_bounds__(H) grad_kernel(const float* __restrict__ p, co
     __syncthreads();
   }
   __syncthreads();
-  for (int i = k; i < H * H; i += H) atomicAdd(&g[OFF_W2 + i], gW2[(i / H) * LD2 + (i % H)]);
+  float* g = partial + (uint64_t)blockIdx.x * NPARAM;
+  for (int i = k; i < H * H; i += H) g[OFF_W2 + i] = gW2[(i / H) * LD2 + (i % H)];
 #pragma unroll
-  for (int i = 0; i < IN; ++i) atomicAdd(&g[OFF_W1 + k * IN + i], gw1[i]);
-  atomicAdd(&g[OFF_B1 + k], gb1);
-  atomicAdd(&g[OFF_B2 + k], gb2);
-  atomicAdd(&g[OFF_W3 + k], gw3);
+  for (int i = 0; i < IN; ++i) g[OFF_W1 + k * IN + i] = gw1[i];
+  g[OFF_B1 + k] = gb1;
+  g[OFF_B2 + k] = gb2;
+  g[OFF_W3 + k] = gw3;
   if (k == 0) {
-    atomicAdd(&g[OFF_B3], gb3);
-    atomicAdd(loss, lsum);
+    g[OFF_B3] = gb3;
+    partial_loss[blockIdx.x] = lsum;
+  }
+}
+
+// g[i] = sum over the CTAs c, in order, of partial[c][i]; *loss likewise.
+__global__ void reduce_kernel(const float* __restrict__ partial, const float* __restrict__ partial_loss, int ctas,
+                              float* __restrict__ g, float* __restrict__ loss) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < NPARAM) {
+    float acc = 0.f;
+    for (int c = 0; c < ctas; ++c) acc += partial[(uint64_t)c * NPARAM + i];
+    g[i] = acc;
+  }
+  if (i == 0) {
+    float l = 0.f;
+    for (int c = 0; c < ctas; ++c) l += partial_loss[c];
+    *loss = l;
   }
 }
 
@@ -281,12 +303,19 @@ gx_status gx_mlp_grad(const float* params, const uint8_t* hist, const float* lab
   gx_status s = set_smem();
   if (s != GX_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  GM_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * gxm::NPARAM, st));
-  GM_CUDA(cudaMemsetAsync(loss, 0, sizeof(float), st));
-  const uint64_t grid = (n + gxm::EPB - 1) / gxm::EPB;
-  gxm::grad_kernel<<<(unsigned)grid, gxm::H, gxm::kGradSmemBytes, st>>>(params, hist, label, n, nullptr,
-                                                                       1.0f / (float)n, grad, loss);
-  GM_CUDA(cudaGetLastError());
+  const int grid = (int)std::min<uint64_t>((n + gxm::EPB - 1) / gxm::EPB, gxm::kGradCtas);
+  float* scratch = nullptr;  // one partial gradient and loss per CTA
+  GM_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(float) * (uint64_t)grid * (gxm::NPARAM + 1), st));
+  gxm::grad_kernel<<<grid, gxm::H, gxm::kGradSmemBytes, st>>>(params, hist, label, n, nullptr, 1.0f / (float)n,
+                                                              scratch, scratch + (uint64_t)grid * gxm::NPARAM);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    gxm::reduce_kernel<<<(gxm::NPARAM + 255) / 256, 256, 0, st>>>(scratch, scratch + (uint64_t)grid * gxm::NPARAM,
+                                                                  grid, grad, loss);
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, std::string("gradient kernels: ") + cudaGetErrorString(e));
   return GX_OK;
 }
 
@@ -298,21 +327,26 @@ gx_status gx_mlp_train(float* params, float* state, const uint8_t* hist, const f
   gx_status s = set_smem();
   if (s != GX_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // state: m | v | g | partial gradients (GX_MLP_GRAD_CTAS x NPARAM) | partial
+  // losses (GX_MLP_GRAD_CTAS) | indices (batch, 8-byte aligned)
   float* m = state;
   float* v = state + gxm::NPARAM;
   float* g = state + 2 * gxm::NPARAM;
-  uint64_t* idx = reinterpret_cast<uint64_t*>(state + 3 * gxm::NPARAM + 1);  // 8-byte aligned below
+  float* partial = state + 3 * gxm::NPARAM;
+  float* partial_loss = partial + (uint64_t)gxm::kGradCtas * gxm::NPARAM;
+  uint64_t* idx = reinterpret_cast<uint64_t*>(partial_loss + gxm::kGradCtas + 1);
   idx = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(idx) + 7) & ~uintptr_t(7));
   GM_CUDA(cudaMemsetAsync(state, 0, sizeof(float) * 3 * gxm::NPARAM, st));
   GM_CUDA(cudaMemsetAsync(loss, 0, sizeof(float) * steps, st));
-  const unsigned grid = (batch + gxm::EPB - 1) / gxm::EPB;
+  const int grid = (int)std::min<uint64_t>((batch + gxm::EPB - 1) / gxm::EPB, gxm::kGradCtas);
   double b1t = 1.0, b2t = 1.0;
   for (uint32_t t = 0; t < steps; ++t) {
     b1t *= 0.9;
     b2t *= 0.999;
     gxm::sample_kernel<<<(batch + 255) / 256, 256, 0, st>>>(idx, batch, n, seed, t);
     gxm::grad_kernel<<<grid, gxm::H, gxm::kGradSmemBytes, st>>>(params, hist, label, batch, idx,
-                                                                1.0f / (float)batch, g, loss + t);
+                                                                1.0f / (float)batch, partial, partial_loss);
+    gxm::reduce_kernel<<<(gxm::NPARAM + 255) / 256, 256, 0, st>>>(partial, partial_loss, grid, g, loss + t);
     gxm::adam_kernel<<<(gxm::NPARAM + 255) / 256, 256, 0, st>>>(params, m, v, g, lr, (float)b1t, (float)b2t);
   }
   GM_CUDA(cudaGetLastError());

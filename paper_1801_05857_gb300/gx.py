@@ -63,8 +63,12 @@ MLP_IN, MLP_HIDDEN = 16, 128
 MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + MLP_HIDDEN + 1
 
 
+MLP_GRAD_CTAS = 256  # GX_MLP_GRAD_CTAS
+
+
 def mlp_state_bytes(batch: int) -> int:
-    return 4 * (3 * MLP_PARAMS + 2) + 8 * batch
+    """GX_MLP_STATE_BYTES(batch)."""
+    return 4 * ((3 + MLP_GRAD_CTAS) * MLP_PARAMS + MLP_GRAD_CTAS + 2) + 8 * batch
 
 
 class gx_stats_t(ctypes.Structure):

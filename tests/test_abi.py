@@ -81,3 +81,13 @@ def test_stats_before_search_is_a_state_error():
 def test_default_opts_values():
     o = gx.default_opts()
     assert (o.bucket_words, o.hash_rounds, o.deadlock_cap, o.warp_cache_log2) == (8, 8, 1024, 9)
+
+
+def test_binding_constants_match_the_header():
+    import re
+    import os
+    from paper_1801_05857_gb300 import build
+    txt = open(os.path.join(build.INCLUDE, "gx.h")).read()
+    assert int(re.search(r"#define GX_MLP_GRAD_CTAS (\d+)", txt).group(1)) == gx.MLP_GRAD_CTAS
+    assert int(re.search(r"#define GX_MLP_IN (\d+)", txt).group(1)) == gx.MLP_IN
+    assert int(re.search(r"#define GX_MLP_HIDDEN (\d+)", txt).group(1)) == gx.MLP_HIDDEN
