@@ -60,11 +60,13 @@ def parse():
     ap.add_argument("--no-table", action="store_true", help="skip the Sec. 5.1 find-or-put part")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided deadlock-search part")
-    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep", "scaled", "scaling-table", "scorer"],
+    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep", "scaled", "scaling-table", "scorer", "batch",
+                             "guided"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
                          "exploration for every (bucket, group) size; scaled: one large token ring; "
                          "scaling-table: ring and producer/consumer families by size (Table 1); "
-                         "scorer: the tensor-core scoring kernel alone; "
+                         "scorer: the tensor-core scoring kernel alone; batch: the 256-network batch "
+                         "alone; guided: one guided search with a host round trip per iteration; "
                          "one JSON line per point")
     return ap.parse_args()
 
@@ -266,13 +268,27 @@ def table_point(torch, gx, keys, n, dup, words, table_words, bucket, group, roun
             "frac_random_gather32": round((n / (ms * 1e-3)) / gather32, 4) if gather32 else None}
 
 
+def table_slots_for(states: int) -> int:
+    """Per-network table of the batch: a power of two of at least 4/3 of the states
+    (<= 75 % fill) and 1024 slots, the rule gx_batch_opts.expected_states applies."""
+    want = max(1024, (states * 4 + 2) // 3)
+    return 1 << (want - 1).bit_length()
+
+
 def batched_part(torch, gx, inputs, steps: int = 5) -> dict:
     """The 256-network batched workload: one graph launch (autotuned) vs one gx_explore
-    per network in sequence.  Tables of 2^21 slots per network (at most 46 % full)."""
+    per network in sequence.  A sizing pass with 2^21-slot tables counts each network's
+    states; the measured runs give every network a table at <= 75 % fill."""
     nets = inputs.batch_workload()
     handles = [gx.load_network(n) for n in nets]
     b = gx.batch_create(handles)
-    o = gx.batch_opts(hash_rounds=32, table_slots=1 << 21)
+    o0 = gx.batch_opts(hash_rounds=32, table_slots=1 << 21)
+    ws0 = gx.batch_alloc_workspace(b, o0)
+    gx.batch_explore(b, o0, ws0)
+    counts = [gx.batch_stats(b, i)["states"] for i in range(len(nets))]
+    del ws0
+    torch.cuda.empty_cache()
+    o = gx.batch_opts(hash_rounds=32, expected_states=counts)
     ws = gx.batch_alloc_workspace(b, o)
     tune_ms = gx.batch_autotune(b, o, ws)
     gx.batch_explore(b, o, ws)
@@ -285,27 +301,28 @@ def batched_part(torch, gx, inputs, steps: int = 5) -> dict:
     trans = sum(gx.batch_stats(b, i)["transitions"] for i in range(len(nets)))
     del ws
     torch.cuda.empty_cache()
-    # sequential: one gx_explore per network, same table size and options
-    wss = {}
-    for h in handles:  # one workspace per slot width, sized for the largest network tables
+    # sequential: one gx_explore per network, with the same per-network table sizes
+    opts2, need = [], {}
+    for h, c in zip(handles, counts):
         w = gx.layout(h)["vector_words"]
         o2 = gx.default_opts(bucket_words=max(o.bucket_words, w), group_lanes=o.group_lanes,
-                             hash_rounds=32, table_bytes=(1 << 21) * 4 * w)
-        need = gx.workspace_bytes(h, o2)
-        if w not in wss or wss[w][1] < need:
-            wss[w] = (o2, need)
-    wss = {w: (o2, torch.empty(need, dtype=torch.uint8, device="cuda")) for w, (o2, need) in wss.items()}
+                             hash_rounds=32, table_bytes=table_slots_for(c) * 4 * w,
+                             frontier_states=table_slots_for(c))
+        opts2.append((w, o2))
+        need[w] = max(need.get(w, 0), gx.workspace_bytes(h, o2))
+    wss = {w: torch.empty(n, dtype=torch.uint8, device="cuda") for w, n in need.items()}
     seq_states = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for h in handles:
-        o2, wsw = wss[gx.layout(h)["vector_words"]]
-        gx.explore(h, o2, wsw)
+    for h, (w, o2) in zip(handles, opts2):
+        gx.explore(h, o2, wss[w])
         seq_states += gx.stats(h)["states"]
     torch.cuda.synchronize()
     seq = time.perf_counter() - t0
     med = ts[len(ts) // 2]
-    return {"networks": len(nets), "states": states, "transitions": trans,
+    bad = [i for i in range(len(nets)) if gx.batch_stats(b, i)["status"] != 0]
+    return {"networks": len(nets), "states": states, "transitions": trans, "failed_networks": bad,
+            "table_slots_total": sum(table_slots_for(c) for c in counts),
             "autotuned": {"bucket_words": o.bucket_words, "group_lanes": o.group_lanes,
                           "chunk_states": o.chunk_states, "tune_best_ms": round(tune_ms, 3)},
             "ms": round(med, 3), "states_per_s": round(states / (med * 1e-3), 1),
@@ -775,6 +792,45 @@ def run_experiment(args):
                     print(json.dumps({"experiment": "sec5.1 find-or-put", **pt}), flush=True)
                     group *= 2
             del keys
+    elif args.experiment == "batch":
+        # the 256-network batch alone, B=8, G=1, 32-state chunks (the autotuner's choice),
+        # tables sized from a first pass: two warm-up launches, then three timed ones
+        nets = inputs.batch_workload()
+        b = gx.batch_create([gx.load_network(n) for n in nets])
+        o0 = gx.batch_opts(hash_rounds=32, table_slots=1 << 21)
+        ws0 = gx.batch_alloc_workspace(b, o0)
+        gx.batch_explore(b, o0, ws0)  # sizing pass: tables at <= 75 % fill below
+        counts = [gx.batch_stats(b, i)["states"] for i in range(len(nets))]
+        del ws0
+        torch.cuda.empty_cache()
+        o = gx.batch_opts(hash_rounds=32, expected_states=counts, bucket_words=8, group_lanes=1, chunk_states=32)
+        ws = gx.batch_alloc_workspace(b, o)
+        for _ in range(2):
+            gx.batch_explore(b, o, ws)
+        ms = []
+        for _ in range(3):
+            gx.batch_explore(b, o, ws)
+            ms.append(gx.batch_stats(b, 0)["gpu_ms"])
+        states = sum(gx.batch_stats(b, i)["states"] for i in range(len(nets)))
+        print(json.dumps({"experiment": "batch", "networks": len(nets), "states": states,
+                          "ms": sorted(ms)[1], "states_per_s": round(states / (sorted(ms)[1] * 1e-3), 1)}), flush=True)
+    elif args.experiment == "guided":
+        # one guided search on planted_network(1, 14, n_traps=2) with one host round trip per
+        # iteration, so that its kernels appear one by one in a launch list
+        from paper_1801_05857_gb300 import guide
+        train_nets = [inputs.planted_network(s, n, n_traps=1 + s % 4) for s in range(6) for n in (6, 7, 8)]
+        hist, label = guide.collect_examples(train_nets, 64)
+        params, _ = guide.train(hist, label, steps=4000, lr=1e-3)
+        net = inputs.planted_network(1, 14, n_traps=2)
+        h = gx.load_network(net)
+        gx.guided_set_weights(h, params)
+        o = gx.default_opts(table_bytes=2 << 30, hash_rounds=32, host_loop=1)
+        ws = gx.guided_alloc_workspace(h, o)
+        n, _ = gx.find_deadlocks(h, gx.GX_DL_GUIDED, o, ws)
+        s = gx.stats(h)
+        print(json.dumps({"experiment": "guided", "network": net.name, "found": n, "explored": s["explored"],
+                          "stored": s["states"], "iterations": s["expand_launches"], "ms": round(s["gpu_ms"], 3)}),
+              flush=True)
     elif args.experiment == "scorer":
         # the tensor-core scorer alone (weights from a seeded initialisation; speed does
         # not depend on their values), 4M random histograms

@@ -415,7 +415,9 @@ gx_status batch_plan(const gx_batch* h, const gx_batch_opts* o, BatchPlan& P) {
                                     : (o->table_slots ? p2ceil(o->table_slots) : (1ull << 20));
     const uint64_t min_slots = std::max<uint64_t>(1024, 2ull * P.B / P.W);
     P.slots[i] = std::max(s, min_slots);
-    P.fcap[i] = std::max<uint64_t>(4096, P.slots[i] / 2);
+    // with expected sizes the ring holds a whole network (slots >= 4/3 of its states), so two
+    // consecutive levels always fit; otherwise half the table
+    P.fcap[i] = std::max<uint64_t>(4096, o->expected_states ? P.slots[i] : P.slots[i] / 2);
   }
   uint64_t off = 0;
   P.off_nets = off;
