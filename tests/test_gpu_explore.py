@@ -249,13 +249,20 @@ def test_warp_cache_too_large_is_rejected(cuda):
     assert e.value.status == gx.GX_ERR_INVALID and "shared memory" in e.value.message
 
 
-def test_mid_config_with_warp_cache(cuda):
+@pytest.mark.parametrize("host_loop", [1, 0])
+def test_mid_config_in_the_benchmark_configuration(cuda, host_loop):
+    """The mid network exactly as bench.py times it (2^28-word table, B=8, G=1, 2^9-entry
+    warp caches, 32 hash-constant sets; the host level loop of its main line, and the
+    device loop it times beside it) against the stored oracle values."""
     g = _golden_case("mid_network.json")
     net = inputs.random_network(**g["generator"])
     h, s, lv, ws = run_gpu(net, table_bytes=4 << 28, bucket_words=8, group_lanes=1, hash_rounds=32,
-                           warp_cache_log2=9)
+                           warp_cache_log2=9, host_loop=host_loop)
     assert (s["states"], s["transitions"], lv) == (g["states"], g["transitions"], g["levels"])
+    assert (s["deadlock_count"], s["deadlock_sum"], s["deadlock_xor"]) == (
+        g["deadlock_count"], g["deadlock_sum"], g["deadlock_xor"])
     assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])
+    assert s["device_levels"] == (0 if host_loop else s["n_levels"])
 
 
 @pytest.mark.parametrize("k", [1, 2, 7, 16, 22])
