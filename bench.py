@@ -556,6 +556,9 @@ def run_ours(args, world, rank, local, pg):
                                  for k, v in rp.items()}
         roof["random_access_unit"] = "G accesses/s, GB/s"
         roof["probes_per_s"] = round(s_avg["probes"] / (exp_ms_per_search * 1e-3) / 1e9, 3)
+        # the bucket reads are random 32-byte accesses: their ceiling is the measured
+        # random-gather rate of the same box, not the sequential copy peak
+        roof["frac_of_random_gather32"] = round(roof["probes_per_s"] / roof["random_access"]["gather32_per_s"], 4)
 
     # the other level loop on the same workload and workspace, timed the same way
     other = None
