@@ -260,6 +260,8 @@ typedef struct gx_stats_t {
   uint64_t device_levels;   /* levels expanded by the device-driven loop */
 } gx_stats_t;
 
+/* Copy the statistics of the last search on `net` into *out (host memory).
+ * GX_ERR_STATE if no search has run on it yet.  Host-only. */
 gx_status gx_stats(const gx_net* net, gx_stats_t* out);
 
 /* Level sizes of the last search: out[k] = number of states at BFS depth k.
@@ -394,6 +396,8 @@ typedef struct gx_batch_opts {
 /* Make a batch from encoded networks (their encodings are copied; the
  * networks may be freed afterwards).  Host-only. */
 gx_status gx_batch_create(const gx_net* const* nets, uint32_t n, gx_batch** out);
+/* Free a batch and its cached graph (NULL is a no-op); the workspace belongs
+ * to the caller. */
 void gx_batch_free(gx_batch* batch);
 
 /* Device workspace bytes for gx_batch_explore with these options. */
@@ -410,6 +414,8 @@ gx_status gx_batch_explore(gx_batch* batch, const gx_batch_opts* opts, void* wor
 
 /* Results of network i in the last gx_batch_explore (gpu_ms is the whole batch). */
 gx_status gx_batch_stats(const gx_batch* batch, uint32_t i, gx_stats_t* out);
+/* Level sizes of network i in the last gx_batch_explore, as gx_levels does for
+ * one network: min(cap, n) entries to out (host), *n_levels the total. */
 gx_status gx_batch_levels(const gx_batch* batch, uint32_t i, uint64_t* out, uint32_t cap,
                           uint32_t* n_levels);
 

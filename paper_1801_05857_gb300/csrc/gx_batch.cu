@@ -572,8 +572,10 @@ gx_status run_batch(gx_batch* h, const gx_batch_opts* o, void* ws, uint64_t ws_b
   }
   GB_CUDA(cudaMemcpyAsync(base + P.off_nets, bn.data(), sizeof(BNet) * n, cudaMemcpyHostToDevice, st));
 
+  // everything the graph holds by value: kernels, launch shapes, and where the
+  // tables it clears start and end (they move when per-network sizes change)
   std::vector<uint64_t> key{(uint64_t)P.B, (uint64_t)P.G, (uint64_t)P.rounds, (uint64_t)P.chunk,
-                            P.levels_cap, P.total};
+                            P.levels_cap, P.total, P.off_tables, P.table_words};
   if (!h->exec || h->exec_ws != ws || h->exec_key != key) {
     s = build_graph(h, P, ws, sms);
     if (s != GX_OK) return s;
