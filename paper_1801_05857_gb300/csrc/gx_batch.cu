@@ -209,6 +209,9 @@ struct BatchOcc {
 
 template <int W, int B, int G>
 __global__ void __launch_bounds__(gx::kBlock, BatchOcc<W, B, G>::min_ctas) batch_expand_kernel(const BatchArgs a) {
+  // a fixed full-size grid: CTAs beyond what this iteration's chunks need leave
+  // before claiming (in the batch's long tail most iterations have few chunks)
+  if ((unsigned long long)blockIdx.x * (gx::kBlock / 32) >= __ldcg(a.prefix + a.n)) return;
   __shared__ uint64_t muls[kMaxRounds];
   for (int i = threadIdx.x; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
