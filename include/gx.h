@@ -85,7 +85,11 @@ typedef struct gx_net gx_net; /* opaque, owned by the library; free with gx_free
  * is reserved (always set in a stored vector, so an all-zero slot is empty);
  * a field never straddles two words.  At most 4 words (3 are padded to 4).
  * Errors: GX_ERR_INVALID for out-of-range states/labels/processes, repeated
- * processes in one rule, empty rules, or vectors longer than 4 words.
+ * processes in one rule, empty rules, rules of more than 16 processes, more
+ * than 124 processes, vectors longer than 4 words, or an upper bound of 2^32
+ * or more on one state's successors (the sum over processes of their most
+ * local edges from one state, plus over rules of the product of their
+ * participants' most matching edges from one state).
  * Host-only: no device memory is touched.  *out is set only on GX_OK. */
 gx_status gx_load_network(const gx_net_desc* desc, gx_net** out);
 

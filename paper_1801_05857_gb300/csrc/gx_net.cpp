@@ -186,6 +186,8 @@ static gx_status encode(const gx_net_desc* d, Net& net) {
     }
     bound = std::min(kSuccCap, bound + prod);
   }
+  // The kernels count one state's successors, and a rule's combinations, in 32 bits.
+  if (bound > 0xFFFFFFFFull) return fail(GX_ERR_INVALID, "a state can have 2^32 or more successors");
   net.max_succ = bound;
   std::vector<uint32_t>& B = net.blob;
   B.clear();

@@ -56,6 +56,11 @@ def test_invalid_networks_are_rejected():
         n.procs.extend([inputs.LTS(1 << 20, 0, []) for _ in range(7)])
     assert "words" in _bad(too_wide)
 
+    def too_many_successors(n):  # 16 processes x 4 parallel edges: 4^16 = 2^32 combinations
+        n.procs.extend([inputs.LTS(2, 0, [(0, 0, 1)] * 4) for _ in range(16)])
+        n.rules.append(inputs.Rule([(p, 0) for p in range(len(n.procs) - 16, len(n.procs))], 0))
+    assert "2^32" in _bad(too_many_successors)
+
 
 def test_workspace_and_option_validation():
     h = gx.load_network(inputs.token_ring(12))          # 2-word vectors
