@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-table", action="store_true", help="skip the Sec. 5.1 find-or-put part")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided deadlock-search part")
-    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "bucket-sweep", "scaled", "scaling-table", "scorer", "batch",
+    ap.add_argument("--experiment", default="", choices=["", "table-sweep", "cuckoo-sweep", "bucket-sweep", "scaled", "scaling-table", "scorer", "batch",
                              "guided"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
                          "exploration for every (bucket, group) size; scaled: one large token ring; "
@@ -265,6 +265,36 @@ def table_point(torch, gx, keys, n, dup, words, table_words, bucket, group, roun
     return {"keys": n, "dup": dup, "bucket_words": bucket, "group_lanes": group, "ms": round(ms, 3),
             "Gkeys_per_s": round(n / (ms * 1e-3) / 1e9, 3),
             "fill": round((n // dup) / (table_words // words), 4),
+            "frac_random_gather32": round((n / (ms * 1e-3)) / gather32, 4) if gather32 else None}
+
+
+def cuckoo_point(torch, gx, keys, n, dup, log2_slots, n_hash, gather32, reps=3):
+    """Cuckoo find-or-put (Sec. 4.1's alternative) of the Sec. 5.1 key sequence into an
+    empty table of 2^log2_slots one-word slots: median device time, and what the lost
+    atomicity costs (keys reported new more than once, keys stored twice)."""
+    st = torch.cuda.current_stream()
+    table = torch.zeros(1 << log2_slots, dtype=torch.int32, device="cuda")
+    counters = torch.zeros(4, dtype=torch.int64, device="cuda")
+    times = []
+    for _ in range(reps + 1):
+        table.zero_()
+        counters.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        gx.cuckoo_find_or_put(keys, 1, table, counters, None, n_hash=n_hash)
+        e1.record(st)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    times = sorted(times[1:])
+    ms = times[len(times) // 2]
+    ins, fnd, fail, exch = counters.cpu().tolist()
+    stored = int((table != 0).sum().item())
+    del table
+    distinct = n // dup
+    return {"table": "cuckoo", "n_hash": n_hash, "keys": n, "dup": dup, "ms": round(ms, 3),
+            "Gkeys_per_s": round(n / (ms * 1e-3) / 1e9, 3), "fill": round(distinct / (1 << log2_slots), 4),
+            "failed": fail, "excess_inserts": ins - distinct, "stored_twice": stored - distinct,
+            "exchanges_per_insert": round(exch / max(ins, 1), 3),
             "frac_random_gather32": round((n / (ms * 1e-3)) / gather32, 4) if gather32 else None}
 
 
@@ -794,6 +824,22 @@ def run_experiment(args):
                     pt = table_point(torch, gx, keys, nd, dup, 1, 1 << 27, bucket, group, 32, g32)
                     print(json.dumps({"experiment": "sec5.1 find-or-put", **pt}), flush=True)
                     group *= 2
+            del keys
+    elif args.experiment == "cuckoo-sweep":
+        # Sec. 4.1's comparison: cuckoo hashing against the bucketed table on the Sec. 5.1
+        # sequences (10^8 one-word keys), both in 2^27 one-word slots (74.5 % full at d = 1)
+        n = 100_000_000
+        rp = random_access_peak(torch, gx)
+        g32 = rp["gather32_per_s"]
+        for dup in (1, 2, 5, 10, 21, 50, 100):
+            nd = n - n % dup
+            keys = table_keys(torch, nd, dup)
+            for k in (3, 4):
+                print(json.dumps({"experiment": "cuckoo vs bucketed", **cuckoo_point(torch, gx, keys, nd, dup, 27, k, g32)}),
+                      flush=True)
+            for bucket in (4, 8):
+                pt = table_point(torch, gx, keys, nd, dup, 1, 1 << 27, bucket, 1, 32, g32)
+                print(json.dumps({"experiment": "cuckoo vs bucketed", "table": "bucketed", **pt}), flush=True)
             del keys
     elif args.experiment == "batch":
         # the 256-network batch alone, B=8, G=1, 32-state chunks (the autotuner's choice),

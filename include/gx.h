@@ -480,6 +480,44 @@ gx_status gx_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t key_wor
                          uint32_t* table, uint64_t table_words, uint8_t* result,
                          uint64_t* counters, void* stream);
 
+/* Cuckoo hashing, the lock-free GPU table Sec. 4.1 weighs against its own
+ * (Alcantara et al.'s GPU form of Pagh & Rodler's cuckoo hashing), for
+ * comparison on the Sec. 5.1 key sequences.  One thread per key:
+ *   1. lookup: the key is present if one of its n_hash positions holds it;
+ *      pos_i(x) = (mix(x) * m_i mod 2^64) >> (64 - log2 table_slots), with
+ *      mix the splitmix64 output function (Steele, Lea & Flood 2014) of the
+ *      stored slot value x (1-word keys: the tagged word; 2-word keys: word 0
+ *      | word 1 << 32, both tagged);
+ *   2. otherwise the key is exchanged into pos_0.  A key y evicted from a slot
+ *      p moves, by exchange, to pos_{(j+1) mod n_hash}(y), j the first index
+ *      with pos_j(y) = p.  The chain ends when an exchange meets an empty slot
+ *      or the key it carries; after max_chain exchanges the key still carried
+ *      is dropped (result 2, counted as failed; the table then lacks a key).
+ * A key being moved sits in no slot, so a concurrent lookup of it misses and
+ * inserts it again: find-or-put can report one key as new more than once and
+ * store it twice.  That is the property Sec. 4.1 finds missing for
+ * state-space exploration.  While nothing failed, the keys stored still form
+ * exactly the input's set, and one key per call gives the sequential
+ * algorithm exactly.
+ *   keys:     device, n_keys * key_words uint32, bit 31 of every word clear.
+ *   key_words: 1 (32-bit slots) or 2 (64-bit slots).
+ *   muls:     host, n_hash odd uint64 multipliers m_i, copied; NULL takes the
+ *             first n_hash hash-constant sets of gx_find_or_put.
+ *   table:    device, table_slots * key_words uint32, 256-byte aligned;
+ *             table_slots a power of two >= 2; zeroed by the caller for an
+ *             empty table; a stored word is the key word | 2^31.
+ *   result:   device, n_keys bytes, or NULL: 1 = inserted, 0 = found (by the
+ *             lookup, or by the first exchange meeting the key), 2 = the chain
+ *             dropped a key.
+ *   counters: device, 4 uint64 (inserted, found, failed, exchanges), added to.
+ * n_hash 2..8 (0 = 4); max_chain 1..4096 (0 = 128).  GX_ERR_INVALID for other
+ * values, an even multiplier, NULL or misaligned pointers.  Asynchronous on
+ * `stream`. */
+gx_status gx_cuckoo_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t key_words,
+                                uint32_t n_hash, uint32_t max_chain, const uint64_t* muls,
+                                uint32_t* table, uint64_t table_slots, uint8_t* result,
+                                uint64_t* counters, void* stream);
+
 /* Random-access probes used as the roofline for the table (no counterpart in
  * the paper): over the largest power-of-two number of `bytes`-sized units that
  * fits a device buffer of `words` uint32, `n` accesses at pseudo-random

@@ -11,6 +11,7 @@ computes and which passages of the paper it follows):
 * ``product_matrix`` -- brute force: the product's transition-count matrix as a
   sum of Kronecker products, and BFS levels by matrix-vector steps (tiny networks)
 * ``mlp``          -- FP64 forward and gradient of the guided search's scoring network
+* ``cuckoo``       -- sequential cuckoo hashing, the table Sec. 4.1 compares with its own
 """
 from __future__ import annotations
 

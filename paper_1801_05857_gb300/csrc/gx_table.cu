@@ -1,5 +1,6 @@
-// C ABI of the isolated hash-table experiment (Sec. 5.1) and of the
-// random-access probes that give the table its roofline.
+// C ABI of the isolated hash-table experiment (Sec. 5.1), of the cuckoo table
+// Sec. 4.1 compares against, and of the random-access probes that give the
+// table its roofline.
 
 #include <string>
 
@@ -63,6 +64,108 @@ probe_cas_kernel(uint32_t* __restrict__ buf, uint64_t unit_mask, int unit_words,
   if ((threadIdx.x & 31) == 0 && acc) atomicXor(sink, (unsigned long long)acc);
 }
 
+// ---- Cuckoo hashing (Pagh & Rodler 2004) in the GPU form of Alcantara et al.,
+// the alternative table Sec. 4.1 weighs against its own.  One thread per key.
+// A slot is one tagged key: 32 bits for 1-word keys, 64 bits for 2-word keys,
+// so a lookup or an exchange is one aligned access.  Position i of a key is
+// (mix64(key) * m_i) >> (64 - log2 slots).
+constexpr int kCuckooMaxHash = 8;
+
+struct CuckooArgs {
+  const uint32_t* keys;
+  uint64_t n;
+  void* table;
+  int log2slots, n_hash, max_chain;
+  uint64_t m[kCuckooMaxHash];
+  uint8_t* result;
+  unsigned long long* counters;  // inserted, found, failed, exchanges
+};
+
+template <int W>
+struct CuckooSlot;
+template <>
+struct CuckooSlot<1> {
+  using T = uint32_t;
+  static __device__ __forceinline__ T pack(const uint32_t* k) { return k[0] | kTag; }
+  static __device__ __forceinline__ uint64_t hash(T x) { return mix64(x); }
+};
+template <>
+struct CuckooSlot<2> {
+  using T = unsigned long long;
+  static __device__ __forceinline__ T pack(const uint32_t* k) {
+    return (T)(k[0] | kTag) | ((T)(k[1] | kTag) << 32);
+  }
+  static __device__ __forceinline__ uint64_t hash(T x) { return mix64(x); }
+};
+
+template <int W>
+__global__ void __launch_bounds__(gx::kBlock) cuckoo_kernel(const CuckooArgs a) {
+  using S = CuckooSlot<W>;
+  using T = typename S::T;
+  T* table = static_cast<T*>(a.table);
+  const int sh = 64 - a.log2slots;
+  const int k = a.n_hash;
+  unsigned long long ins = 0, fnd = 0, fail = 0, exch = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride) {
+    const T key = S::pack(a.keys + i * W);
+    const uint64_t h = S::hash(key);
+    // lookup: the first position alone (where most keys sit), then the others at once
+    bool found = __ldcg(&table[(h * a.m[0]) >> sh]) == key;
+    if (!found) {
+      T s[kCuckooMaxHash];
+#pragma unroll
+      for (int j = 1; j < kCuckooMaxHash; ++j) s[j] = j < k ? __ldcg(&table[(h * a.m[j]) >> sh]) : T(0);
+#pragma unroll
+      for (int j = 1; j < kCuckooMaxHash; ++j) found |= (j < k && s[j] == key);
+    }
+    int r = FOP_FOUND;
+    if (!found) {
+      // insertion: exchange into position 0; an evicted key moves on to the position
+      // after the one it sat in, at most max_chain exchanges in all
+      r = FOP_INSERTED;
+      T x = key;
+      uint64_t pos = (h * a.m[0]) >> sh;
+      int step = 0;
+      for (;; ++step) {
+        if (step == a.max_chain) {  // the key carried now is dropped
+          r = FOP_FULL;
+          break;
+        }
+        const T old = atomicExch(&table[pos], x);
+        if (old == T(0)) break;
+        if (old == x) {  // the slot already held the carried key
+          if (step == 0) r = FOP_FOUND;
+          break;
+        }
+        x = old;
+        const uint64_t ho = S::hash(old);
+        int j = 0;
+        while (j < k - 1 && ((ho * a.m[j]) >> sh) != pos) ++j;
+        j = (j + 1 == k) ? 0 : j + 1;
+        pos = (ho * a.m[j]) >> sh;
+      }
+      exch += (unsigned long long)(step + (r != FOP_FULL));
+    }
+    if (a.result) a.result[i] = (uint8_t)(r == FOP_INSERTED ? 1 : (r == FOP_FOUND ? 0 : 2));
+    ins += r == FOP_INSERTED;
+    fnd += r == FOP_FOUND;
+    fail += r == FOP_FULL;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ins += __shfl_xor_sync(FULLMASK, ins, o);
+    fnd += __shfl_xor_sync(FULLMASK, fnd, o);
+    fail += __shfl_xor_sync(FULLMASK, fail, o);
+    exch += __shfl_xor_sync(FULLMASK, exch, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (ins) atomicAdd(&a.counters[0], ins);
+    if (fnd) atomicAdd(&a.counters[1], fnd);
+    if (fail) atomicAdd(&a.counters[2], fail);
+    if (exch) atomicAdd(&a.counters[3], exch);
+  }
+}
+
 }  // namespace gxd
 
 namespace {
@@ -122,6 +225,56 @@ gx_status gx_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t key_wor
   const uint64_t cap = (uint64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
   const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
   e = ks->fop(a, grid > 0 ? grid : 1, st);
+  if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
+  return GX_OK;
+}
+
+gx_status gx_cuckoo_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t key_words,
+                                uint32_t n_hash, uint32_t max_chain, const uint64_t* muls,
+                                uint32_t* table, uint64_t table_slots, uint8_t* result,
+                                uint64_t* counters, void* stream) {
+  gx::clear_error();
+  if (key_words != 1 && key_words != 2) return gx::fail(GX_ERR_INVALID, "key_words must be 1 or 2");
+  const int k = n_hash ? (int)n_hash : 4;
+  if (k < 2 || k > gxd::kCuckooMaxHash) return gx::fail(GX_ERR_INVALID, "n_hash must be 2..8");
+  const int chain = max_chain ? (int)max_chain : 128;
+  if (chain < 1 || chain > 4096) return gx::fail(GX_ERR_INVALID, "max_chain must be 1..4096");
+  if (!table || !counters || (n_keys && !keys)) return gx::fail(GX_ERR_INVALID, "NULL device pointer");
+  if (reinterpret_cast<uintptr_t>(table) % 256) return gx::fail(GX_ERR_INVALID, "table is not 256-byte aligned");
+  if (table_slots < 2 || (table_slots & (table_slots - 1)))
+    return gx::fail(GX_ERR_INVALID, "table_slots must be a power of two >= 2");
+  gxd::CuckooArgs a{};
+  if (muls) {
+    for (int j = 0; j < k; ++j) {
+      if (!(muls[j] & 1)) return gx::fail(GX_ERR_INVALID, "hash multipliers must be odd");
+      a.m[j] = muls[j];
+    }
+  } else {
+    gx::hash_multipliers(a.m, k);
+  }
+  if (n_keys == 0) return GX_OK;
+  int log2slots = 0;
+  while ((1ull << log2slots) < table_slots) ++log2slots;
+  a.keys = keys;
+  a.n = n_keys;
+  a.table = table;
+  a.log2slots = log2slots;
+  a.n_hash = k;
+  a.max_chain = chain;
+  a.result = result;
+  a.counters = reinterpret_cast<unsigned long long*>(counters);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int per_sm = 0;
+  cudaError_t e = key_words == 1
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gxd::cuckoo_kernel<1>, gx::kBlock, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gxd::cuckoo_kernel<2>, gx::kBlock, 0);
+  if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
+  const uint64_t blocks_needed = (n_keys + gx::kBlock - 1) / gx::kBlock;
+  const uint64_t cap = (uint64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+  const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
+  if (key_words == 1) gxd::cuckoo_kernel<1><<<grid > 0 ? grid : 1, gx::kBlock, 0, st>>>(a);
+  else gxd::cuckoo_kernel<2><<<grid > 0 ? grid : 1, gx::kBlock, 0, st>>>(a);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
   return GX_OK;
 }

@@ -131,6 +131,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "gx_level_profile": ([vp, P(ctypes.c_double), P(u64), P(u64), u32, P(u32)], ctypes.c_int),
         "gx_set_digest": ([vp, vp, u64, vp, P(u64), P(u64), P(u64)], ctypes.c_int),
         "gx_find_or_put": ([vp, u64, u32, u32, u32, u32, vp, u64, vp, vp, vp], ctypes.c_int),
+        "gx_cuckoo_find_or_put": ([vp, u64, u32, u32, u32, vp, vp, u64, vp, vp, vp], ctypes.c_int),
         "gx_probe_random": ([u32, vp, u64, u64, u32, u64, vp, vp], ctypes.c_int),
         "gx_explore_noalloc": ([vp, P(gx_explore_opts), vp, P(gx_stats_t), P(u64), u32, P(u32)],
                                ctypes.c_int),
@@ -558,6 +559,21 @@ def find_or_put(keys, key_words: int, table, counters, result=None, bucket_words
     _check(lib().gx_find_or_put(_ptr(keys), n, key_words, bucket_words, group_lanes, hash_rounds,
                                 _ptr(table), table.numel(), _ptr(result), _ptr(counters),
                                 _stream(stream)))
+
+
+def cuckoo_find_or_put(keys, key_words: int, table, counters, result=None, n_hash: int = 0,
+                       max_chain: int = 0, muls=None, stream=None) -> None:
+    """gx_cuckoo_find_or_put on torch device tensors (keys: 32-bit with n*key_words
+    elements; table: 32-bit with slots*key_words elements, zeroed by the caller;
+    counters: 4 x 64-bit); muls: host sequence of odd multipliers, or None."""
+    n = keys.numel() // key_words
+    m = None
+    if muls is not None:
+        m = np.ascontiguousarray(np.asarray(muls, dtype=np.uint64))
+    _check(lib().gx_cuckoo_find_or_put(_ptr(keys), n, key_words, n_hash, max_chain,
+                                       None if m is None else m.ctypes.data, _ptr(table),
+                                       table.numel() // key_words, _ptr(result), _ptr(counters),
+                                       _stream(stream)))
 
 
 def probe_random(kind: int, buffer, n: int, nbytes: int, seed: int, sink, stream=None) -> None:
