@@ -341,7 +341,9 @@ gx_status gx_training_set(gx_net* net, void* workspace, uint64_t workspace_bytes
 gx_status gx_mlp_init(float* params, uint64_t seed, void* stream);
 
 /* Scores of n examples (hist: device, 16 uint8 each, row-major) into out
- * (device, n floats), on the tensor cores.  Synchronises `stream`.
+ * (device, n floats), on the tensor cores.  Synchronises `stream`.  The
+ * weights are first packed into one library-owned buffer per device, so
+ * concurrent calls from several host threads run one after another.
  * GX_ERR_SPIN_LIMIT if a wait for a tensor-core product timed out. */
 gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, float* out, void* stream);
 

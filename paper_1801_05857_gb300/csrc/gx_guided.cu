@@ -67,7 +67,8 @@ struct GuidedArgs {
   uint32_t batch_cap;
   uint32_t* log;                  // [log_cap] entries
   uint64_t log_cap;
-  const float* params;            // MLP, FP32 (rounded to BF16 when staged)
+  const float* params;            // MLP, FP32
+  gxt::TcWeights* tcw;            // params packed for the scorer, once per search
   uint4* pend_hist;               // [pend_cap] local-state histograms of new states
   uint32_t* pend;                 // [pend_cap] entries of E words (vector, parent)
   uint64_t pend_cap;
@@ -327,44 +328,38 @@ __global__ void __launch_bounds__(gx::kBlock) guided_expand_kernel(const GuidedA
   const unsigned long long log_base = a.ctl->log_base;
   unsigned long long trans = 0, ins = 0;
   uint32_t probes = 0, err = 0;
+  // One warp per state: a batch holds a few thousand states, so the time of an
+  // iteration is the latency of one state's successors; lane l takes
+  // successors l, l + 32, ... and their find-or-puts overlap.
   while (true) {
-    unsigned long long chunk = 0;
-    if (lane == 0) chunk = atomicAdd(&a.ctl->claim, 32ull);
-    chunk = __shfl_sync(FULLMASK, chunk, 0);
-    if (chunk >= n) break;
-    const unsigned long long idx = chunk + lane;
-    const bool valid = idx < n;
+    unsigned long long idx = 0;
+    if (lane == 0) idx = atomicAdd(&a.ctl->claim, 1ull);
+    idx = __shfl_sync(FULLMASK, idx, 0);
+    if (idx >= n) break;
     uint32_t v[W];
-    uint32_t parent = 0;
 #pragma unroll
-    for (int w = 0; w < W; ++w) v[w] = 0;
+    for (int w = 0; w < W; ++w) v[w] = a.batch[idx * E + w];
     const unsigned long long li = log_base + idx;
-    if (valid) {
-#pragma unroll
-      for (int w = 0; w < W; ++w) v[w] = a.batch[idx * E + w];
-      parent = a.batch[idx * E + W];
+    if (lane == 0) {
       uint32_t* le = a.log + li * E;
 #pragma unroll
       for (int w = 0; w < W; ++w) le[w] = v[w];
-      le[W] = parent;
+      le[W] = a.batch[idx * E + W];
     }
-    uint32_t remaining = valid ? count_succ<W>(t, L, v) : 0u;
-    trans += remaining;
-    if (valid && remaining == 0) {
-      atomicMin(&a.ctl->found, li);
-      atomicAdd(&a.ctl->dl_count, 1ull);
-    }
-    SuccIter it;
-    it.init();
-    while (__any_sync(FULLMASK, remaining != 0)) {
-      uint32_t s[W];
-      const bool has = remaining != 0;
-      if (has) {
-        next_succ<W>(it, t, L, v, s);
-        --remaining;
+    const uint32_t total = count_succ<W>(t, L, v);  // the same in every lane
+    if (lane == 0) {
+      trans += total;
+      if (total == 0) {
+        atomicMin(&a.ctl->found, li);
+        atomicAdd(&a.ctl->dl_count, 1ull);
       }
+    }
+    for (uint32_t k0 = 0; k0 < total; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      uint32_t s[W];
       bool inserted = false;
-      if (has) {
+      if (k < total) {
+        seek_succ<W>(t, L, v, k, s);
         const int r = find_or_put<W, B, 1>(a.table, a.log2nb, a.rounds, muls, s, g, probes);
         if (r == FOP_FULL) err |= gx::ERR_TABLE_FULL;
         inserted = r == FOP_INSERTED;
@@ -415,8 +410,13 @@ __global__ void __launch_bounds__(gxt::kRows) guided_score_kernel(const GuidedAr
   if (n > a.pend_cap) n = a.pend_cap;  // the expansion reported the overflow
   const unsigned long long tiles = (n + gxt::kRows - 1) / gxt::kRows;
   if (blockIdx.x >= tiles) return;
-  gxt::TcScorer sc = gxt::tc_setup(tsm, a.params);
+  gxt::TcScorer sc = gxt::tc_setup(tsm, a.tcw);
   uint32_t err = 0;
+  if (!sc.ok) {
+    gxt::tc_teardown(sc);
+    if (threadIdx.x == 0) atomicOr(&a.ctl->error, gx::ERR_SPIN);
+    return;
+  }
   for (unsigned long long tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const unsigned long long row = tile * gxt::kRows + threadIdx.x;
     const bool valid = row < n;
@@ -541,7 +541,8 @@ struct GPlan {
   float scale;
   uint32_t batch_cap;
   uint64_t nb, slots, bin_cap, log_cap, pend_cap;
-  uint64_t off_ctl, off_blob, off_bincnt, off_table, off_bins, off_batch, off_log, off_pend_hist, off_pend, total;
+  uint64_t off_ctl, off_blob, off_tcw, off_bincnt, off_table, off_bins, off_batch, off_log, off_pend_hist, off_pend,
+      total;
   GKernels k;
 };
 
@@ -575,6 +576,8 @@ gx_status guided_plan(const Net& net, const gx_explore_opts* o, GPlan& P) {
   off = a256(off + sizeof(GuidedCtl));
   P.off_blob = off;
   off = a256(off + 4ull * net.blob.size());
+  P.off_tcw = off;
+  off = a256(off + sizeof(gxt::TcWeights));
   P.off_bincnt = off;
   off = a256(off + 8ull * P.nbins);
   P.off_table = off;
@@ -630,6 +633,19 @@ gx_status build_guided_graph(gx_net* h, const GPlan& P, GuidedArgs a, int grid, 
     return e;
   };
   GG_CUDA(add_memset(a.ctl, sizeof(GuidedCtl) / 4));
+  {  // the scorer's weight image, packed once per search
+    const float* pp = a.params;
+    gxt::TcWeights* pw = a.tcw;
+    void* pargs[] = {&pp, &pw};
+    cudaKernelNodeParams kp{};
+    kp.func = reinterpret_cast<void*>(&gxt::tc_pack_kernel);
+    kp.gridDim = dim3(gxt::kTcPackBlocks);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = pargs;
+    cudaGraphNode_t nd;
+    GG_CUDA(cudaGraphAddKernelNode(&nd, g, nullptr, 0, &kp));
+    clears.push_back(nd);
+  }
   GG_CUDA(add_memset(a.bin_count, 2ull * P.nbins));
   const uint64_t words = (uint64_t)P.B * P.nb;
   constexpr uint64_t kPiece = 1ull << 30;
@@ -707,6 +723,7 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
   a.log = reinterpret_cast<uint32_t*>(base + P.off_log);
   a.log_cap = P.log_cap;
   a.params = h->guided_params;
+  a.tcw = reinterpret_cast<gxt::TcWeights*>(base + P.off_tcw);
   a.pend_hist = reinterpret_cast<uint4*>(base + P.off_pend_hist);
   a.pend = reinterpret_cast<uint32_t*>(base + P.off_pend);
   a.pend_cap = P.pend_cap;
@@ -751,6 +768,8 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
     GG_CUDA(cudaMemcpyAsync(ctl, &init, sizeof(init), cudaMemcpyHostToDevice, st));
     GG_CUDA(cudaMemsetAsync(a.bin_count, 0, 8ull * P.nbins, st));
     GG_CUDA(cudaMemsetAsync(a.table, 0, 4ull * P.B * P.nb, st));
+    gxt::tc_pack_kernel<<<gxt::kTcPackBlocks, 256, 0, st>>>(a.params, a.tcw);
+    GG_CUDA(cudaGetLastError());
     void* args[] = {&a};
     GG_CUDA(cudaLaunchKernel(P.k.init, dim3(1), dim3(32), args, 0, st));
     while (true) {

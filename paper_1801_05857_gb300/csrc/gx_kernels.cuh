@@ -115,6 +115,51 @@ __device__ __forceinline__ void next_succ(SuccIter& it, const uint32_t* t, const
   }
 }
 
+// Successor k (k < count_succ) of v, in next_succ's order, without walking
+// the ones before it: O(processes + rules) table reads.  Lets the lanes of a
+// warp take different successors of one state at once.
+template <int W>
+__device__ __forceinline__ void seek_succ(const uint32_t* t, const NetBlobLayout& L, const uint32_t (&v)[W],
+                                          uint32_t k, uint32_t (&out)[W]) {
+#pragma unroll
+  for (int w = 0; w < W; ++w) out[w] = v[w];
+  for (uint32_t p = 0; p < L.n_procs; ++p) {
+    const uint32_t* o = class_range(t, L, p, local_state<W>(t, L, v, p));
+    const uint32_t c = o[1] - o[0];
+    if (k < c) {
+      xor_at<W>(out, t[L.proc_word + p], t[L.cdelta + o[0] + k]);
+      return;
+    }
+    k -= c;
+  }
+  for (uint32_t r = 0; r < L.n_rules; ++r) {
+    const uint32_t j0 = t[L.rule_off + r], j1 = t[L.rule_off + r + 1];
+    uint32_t prod = 1;
+    for (uint32_t j = j0; j < j1 && prod; ++j) {
+      const uint32_t c = t[L.rule_cls + j];
+      const uint32_t* o = class_range(t, L, c, local_state<W>(t, L, v, t[L.cls_proc + c]));
+      prod *= o[1] - o[0];
+    }
+    if (k < prod) {
+      uint32_t x = k;
+      for (uint32_t j = j0; j < j1; ++j) {
+        const uint32_t c = t[L.rule_cls + j];
+        const uint32_t p = t[L.cls_proc + c];
+        const uint32_t* o = class_range(t, L, c, local_state<W>(t, L, v, p));
+        const uint32_t cnt = o[1] - o[0];
+        uint32_t i = 0;
+        if (cnt > 1) {
+          i = x % cnt;
+          x /= cnt;
+        }
+        xor_at<W>(out, t[L.proc_word + p], t[L.cdelta + o[0] + i]);
+      }
+      return;
+    }
+    k -= prod;
+  }
+}
+
 // Order-free digest of one state: h = fold_p mix64(h ^ (p << 32 | s_p)).
 template <int W>
 __device__ __forceinline__ uint64_t state_digest(const uint32_t* t, const NetBlobLayout& L,

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -166,14 +167,22 @@ __global__ void reduce_kernel(const float* __restrict__ partial, const float* __
 
 // Inference on the tensor cores: persistent over tiles of 128 examples.
 __device__ unsigned int g_tc_error;
+// The weights gx_mlp_forward scores with, packed for the tensor cores (one
+// copy per device; calls hold g_forward_mutex from packing to completion).
+__device__ gxt::TcWeights g_tc_packed;
 
-__global__ void __launch_bounds__(gxt::kRows) mlp_tc_forward_kernel(const float* __restrict__ p,
+__global__ void __launch_bounds__(gxt::kRows) mlp_tc_forward_kernel(const gxt::TcWeights* __restrict__ packed,
                                                                      const uint8_t* __restrict__ hist, uint64_t n,
                                                                      float* __restrict__ out) {
   extern __shared__ __align__(16) uint8_t tsm[];
   const uint64_t tiles = (n + gxt::kRows - 1) / gxt::kRows;
   if (blockIdx.x >= tiles) return;
-  gxt::TcScorer sc = gxt::tc_setup(tsm, p);
+  gxt::TcScorer sc = gxt::tc_setup(tsm, packed);
+  if (!sc.ok) {
+    gxt::tc_teardown(sc);
+    if (threadIdx.x == 0) atomicOr(&g_tc_error, 1u);
+    return;
+  }
   for (uint64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const uint64_t row = tile * gxt::kRows + threadIdx.x;
     uint32_t hw[4] = {0, 0, 0, 0};
@@ -272,6 +281,8 @@ gx_status gx_mlp_init(float* params, uint64_t seed, void* stream) {
   return GX_OK;
 }
 
+static std::mutex g_forward_mutex;
+
 gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, float* out, void* stream) {
   gx::clear_error();
   if (!params || (n && (!hist || !out))) return gx::fail(GX_ERR_INVALID, "NULL device pointer");
@@ -286,7 +297,11 @@ gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, f
   const uint64_t grid = std::min<uint64_t>(tiles, (uint64_t)sms * gxt::tc_ctas_per_sm(dev));
   const unsigned int zero = 0;
   GM_CUDA(cudaMemcpyToSymbolAsync(gxm::g_tc_error, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st));
-  gxm::mlp_tc_forward_kernel<<<(unsigned)grid, gxt::kRows, gxt::kTcSmemBytes, st>>>(params, hist, n, out);
+  std::lock_guard<std::mutex> lock(g_forward_mutex);
+  gxt::TcWeights* packed = nullptr;
+  GM_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&packed), gxm::g_tc_packed));
+  gxt::tc_pack_kernel<<<gxt::kTcPackBlocks, 256, 0, st>>>(params, packed);
+  gxm::mlp_tc_forward_kernel<<<(unsigned)grid, gxt::kRows, gxt::kTcSmemBytes, st>>>(packed, hist, n, out);
   GM_CUDA(cudaGetLastError());
   unsigned int err = 0;
   GM_CUDA(cudaMemcpyFromSymbolAsync(&err, gxm::g_tc_error, sizeof(err), 0, cudaMemcpyDeviceToHost, st));

@@ -148,17 +148,29 @@ __host__ __device__ constexpr uint32_t core_offset(uint32_t row, uint32_t k, uin
   return ((row >> 3) * KG + (k >> 3)) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
 }
 
+// The weights of the guide network as a scoring CTA holds them in shared
+// memory: W1 and W2 as BF16 B operands in the core-matrix layout, the FP32
+// biases, w3 rounded to BF16 (kept as FP32) and b3.  One copy per search is
+// packed in global memory by tc_pack_kernel; every CTA then fetches it with a
+// single bulk copy.
+struct __align__(16) TcWeights {
+  uint8_t w1[kHid * kIn * 2];     // B of layer 1 (W1 as N x K), K groups: 2
+  uint8_t w2[kHid * kHid * 2];    // B of layer 2 (W2 as N x K), K groups: 16
+  float b1[kHid], b2[kHid], w3[kHid];
+  float b3, pad[3];
+};
+static_assert(sizeof(TcWeights) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
 // Shared memory of the scorer (dynamic, 1024-byte aligned by the caller).
 struct __align__(1024) TcSmem {
   uint8_t x[kRows * kIn * 2];     // A of layer 1, K groups: 2
-  uint8_t w1[kHid * kIn * 2];     // B of layer 1 (W1 as N x K)
   uint8_t h[kRows * kHid * 2];    // A of layer 2, K groups: 16
-  uint8_t w2[kHid * kHid * 2];    // B of layer 2 (W2 as N x K)
-  float b1[kHid], b2[kHid], w3[kHid];
-  float b3;
+  TcWeights wt;                   // starts 1024-byte aligned (36864)
   uint32_t tmem_slot;
-  unsigned long long mbar;
+  unsigned long long mbar;        // MMA completion
+  unsigned long long mbar_load;   // the weights' bulk copy
 };
+static_assert(sizeof(TcSmem) == 75776, "three scoring CTAs per SM need at most 74 KB each");
 constexpr size_t kTcSmemBytes = sizeof(TcSmem) + 1024;  // + alignment slack
 
 // Scoring CTAs per SM, from the device's shared memory (the occupancy query
@@ -183,56 +195,92 @@ struct TcScorer {
   TcSmem* s;
   uint32_t tmem;
   uint32_t phase;
+  bool ok;  // the weights arrived
 };
 
-// Stage the weights (BF16, round to nearest even) and biases, initialise the
-// barrier and allocate TMEM.  All 128 threads call it.  Parameter layout:
-// W1 (128 x 16) | b1 | W2 (128 x 128) | b2 | w3 | b3, FP32.
-__device__ __forceinline__ TcScorer tc_setup(void* dyn, const float* __restrict__ p) {
-  TcSmem* s = tc_smem(dyn);
-  const int t = threadIdx.x;
+// Packing the weights: BF16 (round to nearest even) for W1, W2 and w3, from
+// the FP32 parameter layout W1 (128 x 16) | b1 | W2 (128 x 128) | b2 | w3 | b3.
+// Thread `item` of a grid of at least kTcPackItems threads writes its part of
+// the packed weights: W1 (256 groups of 8), W2 (2048 groups of 8), one row of
+// b1, b2 and w3 (128), and b3.
+constexpr int kTcPackItems = kHid * 2 + kHid * 16 + kHid + 1;
+__device__ __forceinline__ void tc_pack_item(const float* __restrict__ p, TcWeights* __restrict__ out, int item) {
   const float* pW1 = p;
   const float* pb1 = pW1 + kHid * kIn;
   const float* pW2 = pb1 + kHid;
   const float* pb2 = pW2 + kHid * kHid;
   const float* pw3 = pb2 + kHid;
-  // W1: 128 rows x 2 groups of 8; W2: 128 rows x 16 groups of 8 -- one 16-byte store each
-  for (int c = t; c < kHid * 2; c += kRows) {
-    const int row = c >> 1, g = c & 1;
-    const float* src = pW1 + row * kIn + g * 8;
+  auto group8 = [](const float* src) {
     uint4 q;
     q.x = pack_bf16x2(src[0], src[1]);
     q.y = pack_bf16x2(src[2], src[3]);
     q.z = pack_bf16x2(src[4], src[5]);
     q.w = pack_bf16x2(src[6], src[7]);
-    *reinterpret_cast<uint4*>(s->w1 + core_offset(row, g * 8, 2)) = q;
+    return q;
+  };
+  if (item < kHid * 2) {
+    const int row = item >> 1, g = item & 1;
+    *reinterpret_cast<uint4*>(out->w1 + core_offset(row, g * 8, 2)) = group8(pW1 + row * kIn + g * 8);
+  } else if ((item -= kHid * 2) < kHid * 16) {
+    const int row = item >> 4, g = item & 15;
+    *reinterpret_cast<uint4*>(out->w2 + core_offset(row, g * 8, 16)) = group8(pW2 + row * kHid + g * 8);
+  } else if ((item -= kHid * 16) < kHid) {
+    out->b1[item] = pb1[item];
+    out->b2[item] = pb2[item];
+    out->w3[item] = __bfloat162float(__float2bfloat16_rn(pw3[item]));
+  } else if (item == kHid) {
+    out->b3 = pw3[kHid];
+    out->pad[0] = out->pad[1] = out->pad[2] = 0.f;
   }
-  for (int c = t; c < kHid * 16; c += kRows) {
-    const int row = c >> 4, g = c & 15;
-    const float* src = pW2 + row * kHid + g * 8;
-    uint4 q;
-    q.x = pack_bf16x2(src[0], src[1]);
-    q.y = pack_bf16x2(src[2], src[3]);
-    q.z = pack_bf16x2(src[4], src[5]);
-    q.w = pack_bf16x2(src[6], src[7]);
-    *reinterpret_cast<uint4*>(s->w2 + core_offset(row, g * 8, 16)) = q;
-  }
-  s->b1[t] = pb1[t];
-  s->b2[t] = pb2[t];
-  s->w3[t] = __bfloat162float(__float2bfloat16_rn(pw3[t]));
+}
+
+namespace {
+// Packs the FP32 parameters p into the scorer's weight image (any grid; one
+// item per thread with kTcPackBlocks blocks of 256 threads).
+__global__ void tc_pack_kernel(const float* __restrict__ p, TcWeights* __restrict__ out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kTcPackItems; i += gridDim.x * blockDim.x)
+    tc_pack_item(p, out, i);
+}
+}  // namespace
+constexpr int kTcPackBlocks = (kTcPackItems + 255) / 256;
+
+// Arrive once on mbar and expect `bytes` more from asynchronous copies.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Bulk copy (TMA, no tensor map) of `bytes` from global memory into this
+// CTA's shared memory; both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// Set up a scoring CTA: fetch the packed weights with one bulk copy while
+// warp 0 allocates the TMEM accumulator.  sc.ok is false (in every thread)
+// when the copy did not complete within the bounded wait.
+__device__ __forceinline__ TcScorer tc_setup(void* dyn, const TcWeights* __restrict__ packed) {
+  TcSmem* s = tc_smem(dyn);
+  const int t = threadIdx.x;
   if (t == 0) {
-    s->b3 = pw3[kHid];
     mbar_init(saddr(&s->mbar), 1);
+    mbar_init(saddr(&s->mbar_load), 1);
+    mbar_expect_tx(saddr(&s->mbar_load), (uint32_t)sizeof(TcWeights));
+    bulk_g2s(saddr(&s->wt), packed, (uint32_t)sizeof(TcWeights), saddr(&s->mbar_load));
   }
   if (t < 32) {
+    __syncwarp();  // the allocation is warp-aligned
     tmem_alloc(saddr(&s->tmem_slot), kTmemCols);
     tmem_relinquish();
   }
-  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  return TcScorer{s, s->tmem_slot, 0u};
+  bool ok = mbar_wait_bounded(saddr(&s->mbar_load), 0);
+  if (!ok) ok = mbar_wait_bounded(saddr(&s->mbar_load), 0);  // the copy must land before the CTA leaves
+  const int bad = __syncthreads_or(!ok);
+  return TcScorer{s, s->tmem_slot, 0u, bad == 0};
 }
 
 __device__ __forceinline__ void tc_teardown(const TcScorer& sc) {
@@ -279,7 +327,7 @@ __device__ __forceinline__ bool tc_score_tile(TcScorer& sc, const uint32_t (&hw)
   __syncthreads();
   if (t == 0) {
     tc_fence_after();
-    mma_bf16(sc.tmem, smem_desc(saddr(s->x), 128, 256), smem_desc(saddr(s->w1), 128, 256), 0u);
+    mma_bf16(sc.tmem, smem_desc(saddr(s->x), 128, 256), smem_desc(saddr(s->wt.w1), 128, 256), 0u);
     mma_commit(saddr(&s->mbar));
   }
   if (!tc_wait(sc)) return false;
@@ -294,7 +342,7 @@ __device__ __forceinline__ bool tc_score_tile(TcScorer& sc, const uint32_t (&hw)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int c = c0 + g * 8 + 2 * e;
-        q[e] = pack_bf16x2(fmaxf(acc[g * 8 + 2 * e] + s->b1[c], 0.f), fmaxf(acc[g * 8 + 2 * e + 1] + s->b1[c + 1], 0.f));
+        q[e] = pack_bf16x2(fmaxf(acc[g * 8 + 2 * e] + s->wt.b1[c], 0.f), fmaxf(acc[g * 8 + 2 * e + 1] + s->wt.b1[c + 1], 0.f));
       }
       *reinterpret_cast<uint4*>(s->h + core_offset(t, (uint32_t)(c0 + g * 8), 16)) = make_uint4(q[0], q[1], q[2], q[3]);
     }
@@ -304,7 +352,7 @@ __device__ __forceinline__ bool tc_score_tile(TcScorer& sc, const uint32_t (&hw)
   __syncthreads();
   if (t == 0) {
     tc_fence_after();
-    const uint32_t ha = saddr(s->h), wa = saddr(s->w2);
+    const uint32_t ha = saddr(s->h), wa = saddr(s->wt.w2);
 #pragma unroll
     for (uint32_t kk = 0; kk < kHid / 16; ++kk)
       mma_bf16(sc.tmem, smem_desc(ha + 256u * kk, 128, 2048), smem_desc(wa + 256u * kk, 128, 2048), kk > 0 ? 1u : 0u);
@@ -312,13 +360,13 @@ __device__ __forceinline__ bool tc_score_tile(TcScorer& sc, const uint32_t (&hw)
   }
   if (!tc_wait(sc)) return false;
   // layer-2 epilogue: y = b3 + w3 . relu(A2 + b2)
-  float acc_y = s->b3;
+  float acc_y = s->wt.b3;
 #pragma unroll 1
   for (int c0 = 0; c0 < kHid; c0 += 32) {
     float acc[32];
     tmem_ld32(sc.tmem + lane_base + (uint32_t)c0, acc);
 #pragma unroll
-    for (int e = 0; e < 32; ++e) acc_y += s->w3[c0 + e] * fmaxf(acc[e] + s->b2[c0 + e], 0.f);
+    for (int e = 0; e < 32; ++e) acc_y += s->wt.w3[c0 + e] * fmaxf(acc[e] + s->wt.b2[c0 + e], 0.f);
   }
   y = acc_y;
   // our TMEM reads and the tile's shared-memory use end before the next tile starts
