@@ -396,8 +396,12 @@ typedef struct gx_batch_opts {
   const uint64_t* expected_states; /* optional host array, one entry per network: network i
                                gets a table of at least expected_states[i] / 0.75 slots */
   uint32_t levels_cap;      /* BFS levels kept per network; 0 = 4096 */
-  uint32_t reserved;
+  uint32_t wide_factor;     /* an iteration with at most wide_factor x (warps of the
+                               expansion grid) states, over all networks, expands one
+                               warp per state (lane l takes successors l, l + 32, ...);
+                               0 = 4; GX_BATCH_WIDE_OFF: never */
 } gx_batch_opts;
+#define GX_BATCH_WIDE_OFF 0xFFFFFFFFu
 
 /* Make a batch from encoded networks (their encodings are copied; the
  * networks may be freed afterwards).  Host-only. */

@@ -49,6 +49,8 @@ struct BatchArgs {
   unsigned long long* prefix;  // n + 1 entries
   unsigned long long* claim;
   unsigned long long* iters;   // iterations of the WHILE loop so far
+  unsigned long long* unit;    // states per claim this iteration: chunk, or 1 (one warp per state)
+  unsigned long long wide_states;  // iterations with at most this many states use unit 1
   unsigned long long max_iters;
   cudaGraphConditionalHandle cond;
 };
@@ -95,31 +97,48 @@ __global__ void __launch_bounds__(gx::kBlock) batch_init_kernel(const BatchArgs 
 // next iteration's chunks.
 __global__ void __launch_bounds__(1024) batch_advance_kernel(const BatchArgs a, int first) {
   __shared__ unsigned long long warp_tot[32];
-  __shared__ unsigned long long carry;
+  __shared__ unsigned long long carry, s_unit;
   if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // 1. close the level just expanded and count the states of the next one
+  unsigned long long states = 0;
+  for (int i = threadIdx.x; i < a.n; i += blockDim.x) {
+    BNet& b = a.nets[i];
+    if (!first && b.active) {
+      const unsigned long long fresh = b.next_end - b.cur_end;
+      if (b.dl_count > 0 && b.first_dl < 0) b.first_dl = (int)b.n_levels - 1;
+      if (fresh > 0) {
+        if (b.n_levels < b.levels_cap) b.levels[b.n_levels] = fresh;
+        else b.error |= gx::ERR_LEVELS;
+        b.n_levels += 1;
+      }
+      if (b.error || fresh == 0) {
+        b.active = 0;
+      } else {
+        b.cur_begin = b.cur_end;
+        b.cur_end = b.next_end;
+      }
+    }
+    if (b.active) states += b.cur_end - b.cur_begin;
+  }
+  states = warp_sum(states);
+  if (lane == 0) warp_tot[wid] = states;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < (int)(blockDim.x / 32); ++w) tot += warp_tot[w];
+    // few states in all: give each one a warp, so that its successors' lookups overlap
+    s_unit = tot <= a.wide_states ? 1ull : (unsigned long long)a.chunk;
+  }
+  __syncthreads();
+  const unsigned long long unit = s_unit;
+  // 2. claims per network and their exclusive prefix sums
   for (int base = 0; base < a.n; base += blockDim.x) {
     const int i = base + threadIdx.x;
     unsigned long long chunks = 0;
     if (i < a.n) {
-      BNet& b = a.nets[i];
-      if (!first && b.active) {
-        const unsigned long long fresh = b.next_end - b.cur_end;
-        if (b.dl_count > 0 && b.first_dl < 0) b.first_dl = (int)b.n_levels - 1;
-        if (fresh > 0) {
-          if (b.n_levels < b.levels_cap) b.levels[b.n_levels] = fresh;
-          else b.error |= gx::ERR_LEVELS;
-          b.n_levels += 1;
-        }
-        if (b.error || fresh == 0) {
-          b.active = 0;
-        } else {
-          b.cur_begin = b.cur_end;
-          b.cur_end = b.next_end;
-        }
-      }
-      if (b.active) chunks = (b.cur_end - b.cur_begin + a.chunk - 1) / a.chunk;
+      const BNet& b = a.nets[i];
+      if (b.active) chunks = (b.cur_end - b.cur_begin + unit - 1) / unit;
     }
     // block-wide inclusive scan of chunks
     unsigned long long inc = chunks;
@@ -164,6 +183,7 @@ __global__ void __launch_bounds__(1024) batch_advance_kernel(const BatchArgs a, 
     }
     a.prefix[a.n] = carry;
     *a.claim = 0;
+    *a.unit = unit;
     cudaGraphSetConditional(a.cond, more ? 1u : 0u);
   }
 }
@@ -228,6 +248,7 @@ __global__ void __launch_bounds__(gx::kBlock, BatchOcc<W, B, G>::min_ctas) batch
   __shared__ unsigned long long s_chunk[gx::kBlock / 32][2];  // [first, end) of the warp's chunk
   unsigned long long* chunk_range = s_chunk[threadIdx.x >> 5];
   constexpr int K = PerLane<G>::K;
+  const unsigned long long unit = __ldcg(a.unit);  // 1: one warp per state this iteration
   while (true) {
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(a.claim, 1ull);
@@ -261,44 +282,56 @@ __global__ void __launch_bounds__(gx::kBlock, BatchOcc<W, B, G>::min_ctas) batch
     const NetBlobLayout& L = wn.lay;
     const SmemTarget tg{&wn, a.rounds};
     if (lane == 0) {
-      const uint64_t first = wn.cur_begin + (c - __ldcg(a.prefix + lo)) * (uint64_t)a.chunk;
+      const uint64_t first = wn.cur_begin + (c - __ldcg(a.prefix + lo)) * unit;
       const uint64_t end = b.cur_end;
       chunk_range[0] = first;
-      chunk_range[1] = first + a.chunk < end ? first + a.chunk : end;
+      chunk_range[1] = first + unit < end ? first + unit : end;
     }
     __syncwarp();
-    uint32_t trans = 0;  // per chunk: far below 2^32
+    uint32_t trans = 0;  // per claim: below 2^32 (a state's successors are, and chunks stay far below)
     uint32_t probes = 0, err = 0;
+    // Lane layout: one state per lane (unit > 1), or, in an iteration with few
+    // states, one state per warp (unit == 1): every lane holds the state and
+    // takes its successors l, l + 32, ... (found by index), so their
+    // find-or-puts overlap instead of forming one lane's chain.
+    static_assert(K == 1, "one successor per lane and round");
+    const bool wide = unit == 1;
     for (uint64_t sub = chunk_range[0]; sub < chunk_range[1]; sub += 32) {
-      const uint64_t idx = sub + lane;
+      const uint64_t idx = wide ? sub : sub + lane;
       const bool valid = idx < chunk_range[1];
       uint32_t v[W];
 #pragma unroll
       for (int w = 0; w < W; ++w) v[w] = 0;
       if (valid) load_vec<W>(wn.frontier + (idx & wn.fmask) * W, v);
-      uint32_t remaining = valid ? count_succ<W>(t, L, v) : 0u;
-      trans += remaining;
-      if (valid && remaining == 0) {
-        const uint64_t h = state_digest<W>(t, L, v);
-        atomicAdd(&b.dl_count, 1ull);
-        atomicAdd(&b.dl_sum, (unsigned long long)h);
-        atomicXor(&b.dl_xor, (unsigned long long)h);
+      const uint32_t cnt = valid ? count_succ<W>(t, L, v) : 0u;
+      if (valid && (!wide || lane == 0)) {  // the lane that accounts for the state
+        trans += cnt;
+        if (cnt == 0) {
+          const uint64_t h = state_digest<W>(t, L, v);
+          atomicAdd(&b.dl_count, 1ull);
+          atomicAdd(&b.dl_sum, (unsigned long long)h);
+          atomicXor(&b.dl_xor, (unsigned long long)h);
+        }
       }
+      uint32_t remaining = !wide ? cnt : (cnt > (uint32_t)lane ? (cnt - lane + 31) / 32 : 0u);
+      uint32_t kk = lane;  // wide: index of this lane's next successor
       SuccIter it;
       it.init();
       while (__any_sync(FULLMASK, remaining != 0)) {
         uint32_t s[K][W];
         bool has[K];
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          has[k] = remaining != 0;
-          if (has[k]) {
-            next_succ<W>(it, t, L, v, s[k]);
-            --remaining;
+        has[0] = remaining != 0;
+        if (has[0]) {
+          if (wide) {
+            seek_succ<W>(t, L, v, kk, s[0]);
+            kk += 32;
           } else {
-#pragma unroll
-            for (int w = 0; w < W; ++w) s[k][w] = 0;
+            next_succ<W>(it, t, L, v, s[0]);
           }
+          --remaining;
+        } else {
+#pragma unroll
+          for (int w = 0; w < W; ++w) s[0][w] = 0;
         }
         insert_lanes<W, B, G, K>(tg, muls, g, has, s, probes, err, st, cache);
       }
@@ -360,7 +393,7 @@ inline uint64_t p2ceil(uint64_t x) {
 
 struct BatchPlan {
   int W = 0, B = 0, G = 0, rounds = 0, chunk = 0;
-  uint32_t levels_cap = 0;
+  uint32_t levels_cap = 0, wide = 0;
   std::vector<uint64_t> slots, fcap;
   uint64_t off_nets = 0, off_prefix = 0, off_claim = 0, off_blobs = 0, off_levels = 0,
            off_fronts = 0, off_tables = 0, table_words = 0, total = 0;
@@ -411,6 +444,7 @@ gx_status batch_plan(const gx_batch* h, const gx_batch_opts* o, BatchPlan& P) {
     return fail(GX_ERR_INVALID, "no batch kernel for bucket_words " + std::to_string(P.B) + ", group_lanes " +
                                     std::to_string(P.G) + " with " + std::to_string(P.W) + "-word slots");
   P.levels_cap = o->levels_cap ? o->levels_cap : 4096;
+  P.wide = o->wide_factor ? o->wide_factor : 4u;
   P.slots.resize(n);
   P.fcap.resize(n);
   for (uint32_t i = 0; i < n; ++i) {
@@ -428,7 +462,7 @@ gx_status batch_plan(const gx_batch* h, const gx_batch_opts* o, BatchPlan& P) {
   P.off_prefix = off;
   off = a256(off + 8ull * (n + 1));
   P.off_claim = off;
-  off = a256(off + 16);  // claim counter, iteration counter
+  off = a256(off + 24);  // claim counter, iteration counter, states per claim
   P.off_blobs = off;
   P.blob_off.resize(n);
   for (uint32_t i = 0; i < n; ++i) {
@@ -471,6 +505,10 @@ gx_status build_graph(gx_batch* h, const BatchPlan& P, void* ws, int sms) {
   cudaGraphConditionalHandle cond;
   GB_CUDA(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
 
+  int per_sm = 0;
+  GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.k.expand, kBlock, 0));
+  const int grid = sms * std::max(per_sm, 1);
+
   BatchArgs a{};
   a.nets = reinterpret_cast<BNet*>(base + P.off_nets);
   a.n = n;
@@ -480,6 +518,8 @@ gx_status build_graph(gx_batch* h, const BatchPlan& P, void* ws, int sms) {
   a.prefix = reinterpret_cast<unsigned long long*>(base + P.off_prefix);
   a.claim = reinterpret_cast<unsigned long long*>(base + P.off_claim);
   a.iters = a.claim + 1;
+  a.unit = a.claim + 2;
+  a.wide_states = P.wide == GX_BATCH_WIDE_OFF ? 0ull : (unsigned long long)P.wide * grid * (kBlock / 32);
   a.max_iters = (unsigned long long)P.levels_cap + 1;
   a.cond = cond;
 
@@ -524,9 +564,6 @@ gx_status build_graph(gx_batch* h, const BatchPlan& P, void* ws, int sms) {
   GB_CUDA(cudaGraphAddNode(&cnode, g, &adv1, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
 
-  int per_sm = 0;
-  GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.k.expand, kBlock, 0));
-  const int grid = sms * std::max(per_sm, 1);
   cudaGraphNode_t ex, adv0;
   GB_CUDA(add_kernel(body, nullptr, 0, P.k.expand, dim3(grid), dim3(kBlock), args_a, &ex));
   GB_CUDA(add_kernel(body, &ex, 1, reinterpret_cast<const void*>(&gxd::batch_advance_kernel), dim3(1),
@@ -578,7 +615,7 @@ gx_status run_batch(gx_batch* h, const gx_batch_opts* o, void* ws, uint64_t ws_b
   // everything the graph holds by value: kernels, launch shapes, and where the
   // tables it clears start and end (they move when per-network sizes change)
   std::vector<uint64_t> key{(uint64_t)P.B, (uint64_t)P.G, (uint64_t)P.rounds, (uint64_t)P.chunk,
-                            P.levels_cap, P.total, P.off_tables, P.table_words};
+                            P.levels_cap, P.total, P.off_tables, P.table_words, P.wide};
   if (!h->exec || h->exec_ws != ws || h->exec_key != key) {
     s = build_graph(h, P, ws, sms);
     if (s != GX_OK) return s;

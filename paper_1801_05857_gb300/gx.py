@@ -88,7 +88,7 @@ class gx_stats_t(ctypes.Structure):
 class gx_batch_opts(ctypes.Structure):
     _fields_ = [("bucket_words", u32), ("group_lanes", u32), ("hash_rounds", u32),
                 ("chunk_states", u32), ("table_slots", u64), ("expected_states", P(u64)),
-                ("levels_cap", u32), ("reserved", u32)]
+                ("levels_cap", u32), ("wide_factor", u32)]
 
 
 _lib = None
