@@ -262,50 +262,65 @@ __global__ void __launch_bounds__(32) guided_init_kernel(const GuidedArgs a) {
   if (err) atomicOr(&a.ctl->error, err);
 }
 
-// One CTA: pop the next batch from the best non-empty bin.
+// Pop the next batch from the best non-empty bin (one CTA of up to 1024
+// threads, all calling).  The bins are scanned in parallel, one counter per
+// thread.  Returns (in every thread) whether a batch was taken; sets done
+// when every bin is empty.
 template <int W>
-__global__ void __launch_bounds__(1024) guided_select_kernel(const GuidedArgs a) {
+__device__ __forceinline__ bool select_batch(const GuidedArgs& a) {
   constexpr int E = W + 1;
   __shared__ int best;
   __shared__ unsigned long long take, top;
+  GuidedCtl& c = *a.ctl;
+  const bool go = c.found == ~0ull && !c.error;  // uniform: read before anyone writes
+  __syncthreads();
   if (threadIdx.x == 0) {
-    best = -1;
-    GuidedCtl& c = *a.ctl;
+    best = 0x7FFFFFFF;
     c.batch_n = 0;
     c.claim = 0;
     c.pending = 0;
-    if (c.found == ~0ull && !c.error) {
-      for (int b = 0; b < a.nbins; ++b) {
-        unsigned long long cnt = a.bin_count[b];
-        if (cnt > a.bin_cap) cnt = a.bin_cap;  // failed pushes left the counter past the end
-        a.bin_count[b] = cnt;
-        if (cnt > 0) {
-          best = b;
-          break;
-        }
-      }
-      if (best < 0) {
-        c.done = 1;
+  }
+  __syncthreads();
+  if (!go) return false;
+  for (int b = threadIdx.x; b < a.nbins; b += blockDim.x) {
+    unsigned long long cnt = a.bin_count[b];
+    if (cnt > a.bin_cap) {  // failed pushes left the counter past the end
+      cnt = a.bin_cap;
+      a.bin_count[b] = cnt;
+    }
+    if (cnt > 0) atomicMin(&best, b);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (best == 0x7FFFFFFF) {
+      c.done = 1;
+      best = -1;
+    } else {
+      const unsigned long long cnt = a.bin_count[best];
+      take = cnt < a.batch_cap ? cnt : a.batch_cap;
+      top = cnt - take;
+      if (c.log_count + take > a.log_cap) {
+        c.error |= gx::ERR_LOG;
+        best = -1;
       } else {
-        const unsigned long long cnt = a.bin_count[best];
-        take = cnt < a.batch_cap ? cnt : a.batch_cap;
-        top = cnt - take;
-        if (c.log_count + take > a.log_cap) {
-          c.error |= gx::ERR_LOG;
-          best = -1;
-        } else {
-          a.bin_count[best] = top;
-          c.batch_n = take;
-          c.log_base = c.log_count;
-          c.log_count += take;
-        }
+        a.bin_count[best] = top;
+        c.batch_n = take;
+        c.log_base = c.log_count;
+        c.log_count += take;
       }
     }
   }
   __syncthreads();
-  if (best < 0) return;
+  if (best < 0) return false;
   const uint32_t* src = a.bins + ((uint64_t)best * a.bin_cap + top) * E;
   for (uint64_t i = threadIdx.x; i < take * E; i += blockDim.x) a.batch[i] = src[i];
+  return true;
+}
+
+// One CTA: pop the next batch (the host-driven loop).
+template <int W>
+__global__ void __launch_bounds__(1024) guided_select_kernel(const GuidedArgs a) {
+  select_batch<W>(a);
 }
 
 template <int W, int B>
@@ -450,18 +465,30 @@ __global__ void __launch_bounds__(gxt::kRows) guided_score_kernel(const GuidedAr
 // Control block at the start of a search (the rest was cleared).
 __global__ void guided_reset_kernel(const GuidedArgs a) { a.ctl->found = ~0ull; }
 
-__global__ void guided_loop_start_kernel(const GuidedArgs a) {
-  cudaGraphSetConditional(a.cond, a.ctl->error ? 0u : 1u);
+// Start of the device-driven loop (one CTA of 1024 threads): pop the first
+// batch; the loop runs if there is one.
+template <int W>
+__global__ void __launch_bounds__(1024) guided_loop_start_kernel(const GuidedArgs a) {
+  const bool more = select_batch<W>(a);
+  if (threadIdx.x == 0) cudaGraphSetConditional(a.cond, more ? 1u : 0u);
 }
 
-// After {select, expand, score}: go on unless a deadlock was found, the open
-// set is empty, an error occurred or the iteration bound (every iteration
-// expands at least one state, so the log size bounds it) was reached.
-__global__ void guided_advance_kernel(const GuidedArgs a) {
+// After {expand, score}: go on unless a deadlock was found, the open set is
+// empty, an error occurred or the iteration bound (every iteration expands at
+// least one state, so the log size bounds it) was reached -- and if going on,
+// pop the next batch here, so that an iteration takes three kernels.
+template <int W>
+__global__ void __launch_bounds__(1024) guided_advance_kernel(const GuidedArgs a) {
   GuidedCtl& c = *a.ctl;
-  c.iters += 1;
-  const bool more = c.found == ~0ull && !c.done && !c.error && c.iters < a.max_iters;
-  cudaGraphSetConditional(a.cond, more ? 1u : 0u);
+  __shared__ int s_more;
+  if (threadIdx.x == 0) {
+    c.iters += 1;
+    s_more = c.found == ~0ull && !c.done && !c.error && c.iters < a.max_iters;
+  }
+  __syncthreads();
+  bool more = s_more != 0;
+  if (more) more = select_batch<W>(a);
+  if (threadIdx.x == 0) cudaGraphSetConditional(a.cond, more ? 1u : 0u);
 }
 
 // One thread: follow the parent log indices from the deadlock back to the
@@ -509,6 +536,8 @@ struct GKernels {
   const void* expand;
   const void* score;
   const void* path;
+  const void* start;    // pop the first batch and start the device loop
+  const void* advance;  // end an iteration and pop the next batch
 };
 
 template <int W, int B>
@@ -517,7 +546,9 @@ GKernels gk() {
                   reinterpret_cast<const void*>(&gxd::guided_select_kernel<W>),
                   reinterpret_cast<const void*>(&gxd::guided_expand_kernel<W, B>),
                   reinterpret_cast<const void*>(&gxd::guided_score_kernel<W>),
-                  reinterpret_cast<const void*>(&gxd::guided_path_kernel<W>)};
+                  reinterpret_cast<const void*>(&gxd::guided_path_kernel<W>),
+                  reinterpret_cast<const void*>(&gxd::guided_loop_start_kernel<W>),
+                  reinterpret_cast<const void*>(&gxd::guided_advance_kernel<W>)};
 }
 
 bool gk_lookup(int W, int B, GKernels& k) {
@@ -609,7 +640,8 @@ void release_guided(gx_net* h) {
 namespace {
 
 // One guided search as a graph: clear the control block, bins and table,
-// insert the initial state, then WHILE(cond) {select, expand, score, advance}.
+// insert the initial state, pop the first batch, then WHILE(cond) {expand,
+// score, advance (which pops the next batch)}.
 gx_status build_guided_graph(gx_net* h, const GPlan& P, GuidedArgs a, int grid, size_t smem, int score_grid) {
   release_guided(h);
   h->release_guided = &release_guided;
@@ -661,12 +693,11 @@ gx_status build_guided_graph(gx_net* h, const GPlan& P, GuidedArgs a, int grid, 
     kp.kernelParams = args;
     return cudaGraphAddKernelNode(out, gr, deps, nd, &kp);
   };
-  cudaGraphNode_t reset, init, start, sel, ex, sc, adv, cnode;
+  cudaGraphNode_t reset, init, start, ex, sc, adv, cnode;
   GG_CUDA(add_kernel(g, clears.data(), clears.size(), reinterpret_cast<const void*>(&gxd::guided_reset_kernel),
                      dim3(1), dim3(1), 0, &reset));
   GG_CUDA(add_kernel(g, &reset, 1, P.k.init, dim3(1), dim3(32), 0, &init));
-  GG_CUDA(add_kernel(g, &init, 1, reinterpret_cast<const void*>(&gxd::guided_loop_start_kernel), dim3(1), dim3(1), 0,
-                     &start));
+  GG_CUDA(add_kernel(g, &init, 1, P.k.start, dim3(1), dim3(1024), 0, &start));
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = cond;
@@ -674,11 +705,9 @@ gx_status build_guided_graph(gx_net* h, const GPlan& P, GuidedArgs a, int grid, 
   cp.conditional.size = 1;
   GG_CUDA(cudaGraphAddNode(&cnode, g, &start, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  GG_CUDA(add_kernel(body, nullptr, 0, P.k.select, dim3(1), dim3(1024), 0, &sel));
-  GG_CUDA(add_kernel(body, &sel, 1, P.k.expand, dim3(grid), dim3(kBlock), smem, &ex));
+  GG_CUDA(add_kernel(body, nullptr, 0, P.k.expand, dim3(grid), dim3(kBlock), smem, &ex));
   GG_CUDA(add_kernel(body, &ex, 1, P.k.score, dim3(score_grid), dim3(gxt::kRows), gxt::kTcSmemBytes, &sc));
-  GG_CUDA(add_kernel(body, &sc, 1, reinterpret_cast<const void*>(&gxd::guided_advance_kernel), dim3(1), dim3(1), 0,
-                     &adv));
+  GG_CUDA(add_kernel(body, &sc, 1, P.k.advance, dim3(1), dim3(1024), 0, &adv));
   cudaGraphExec_t exec;
   GG_CUDA(cudaGraphInstantiate(&exec, g, 0));
   h->guided_exec = exec;
