@@ -331,7 +331,10 @@ gx_status gx_set_digest(gx_net* net, void* workspace, uint64_t workspace_bytes, 
  * 16 uint8 per example) and label_out (device, float: min(distance, max_dist)
  * / max_dist, 1.0 when no deadlock is reachable).  dist_scratch: device, one
  * uint32 per table slot (gx_stats table_slots).  *n_out = states found (may
- * exceed cap).  GX_ERR_INVALID if a process has more than 16 local states. */
+ * exceed cap).  The examples come sorted by content (the 16 histogram bytes,
+ * then the label's bits, as unsigned words), so with cap >= *n_out the output
+ * is the same on every run.  GX_ERR_INVALID if a process has more than 16
+ * local states. */
 gx_status gx_training_set(gx_net* net, void* workspace, uint64_t workspace_bytes, void* stream,
                           uint32_t* dist_scratch, uint32_t max_dist, uint8_t* hist_out,
                           float* label_out, uint64_t cap, uint64_t* n_out);

@@ -7,7 +7,9 @@
 // relaxation -- distance 0 for states without successors, distance r for a
 // state with a successor at distance r - 1 -- looking successors up in the
 // same table.  Then each state becomes one example: the histogram of its
-// processes' local states and the capped, normalised distance.
+// processes' local states and the capped, normalised distance, and the
+// examples are sorted by content so that the set comes out the same way on
+// every run.
 //
 // Guided search (gx_find_deadlocks, GX_DL_GUIDED): open states live in
 // priority bins (stacks) by score.  Each iteration:
@@ -186,6 +188,58 @@ __global__ void __launch_bounds__(gx::kBlock) label_sweep_kernel(const uint32_t*
     }
   }
   if (__any_sync(FULLMASK, any != 0) && (threadIdx.x & 31) == 0) atomicAdd(changed, 1ull);
+}
+
+// Content order of the training examples: the gather appends at atomic
+// positions, so the examples are sorted by their own content (the 16
+// histogram bytes, then the label's bits, compared as unsigned words) to make
+// the training set -- and everything trained from it -- the same on every run.
+// Equal keys are identical examples, so an unstable sort is enough: a bitonic
+// sort over a power-of-two buffer padded with all-ones keys (no histogram byte
+// reaches 0xFF).
+__device__ __forceinline__ bool ex_greater(const uint4& a, uint32_t la, const uint4& b, uint32_t lb) {
+  if (a.x != b.x) return a.x > b.x;
+  if (a.y != b.y) return a.y > b.y;
+  if (a.z != b.z) return a.z > b.z;
+  if (a.w != b.w) return a.w > b.w;
+  return la > lb;
+}
+
+__global__ void ex_load_kernel(const uint8_t* hist, const float* label, uint64_t n, uint64_t n2, uint4* h,
+                               uint32_t* l) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (uint64_t)gridDim.x * blockDim.x) {
+    if (i < n) {
+      h[i] = reinterpret_cast<const uint4*>(hist)[i];
+      l[i] = __float_as_uint(label[i]);
+    } else {
+      h[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
+      l[i] = ~0u;
+    }
+  }
+}
+
+// One compare-exchange pass of the bitonic network: stage k, distance j.
+__global__ void ex_bitonic_kernel(uint4* h, uint32_t* l, uint64_t n2, uint64_t k, uint64_t j) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t p = i ^ j;
+    if (p <= i) continue;
+    const uint4 a = h[i], b = h[p];
+    const uint32_t la = l[i], lb = l[p];
+    const bool up = (i & k) == 0;
+    if (up == ex_greater(a, la, b, lb)) {
+      h[i] = b;
+      h[p] = a;
+      l[i] = lb;
+      l[p] = la;
+    }
+  }
+}
+
+__global__ void ex_store_kernel(const uint4* h, const uint32_t* l, uint64_t n, uint8_t* hist, float* label) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    reinterpret_cast<uint4*>(hist)[i] = h[i];
+    label[i] = __uint_as_float(l[i]);
+  }
 }
 
 template <int W>
@@ -983,6 +1037,26 @@ gx_status gx_training_set(gx_net* h, void* ws, uint64_t ws_bytes, void* stream, 
   GG_CUDA(cudaStreamSynchronize(st));
   if (n_out) *n_out = res[0];
   if (res[1]) return gx::fail(GX_ERR_INVALID, "a process has a local state index of 16 or more");
+  // content order (see ex_bitonic_kernel)
+  const uint64_t m = std::min<uint64_t>(res[0], cap);
+  if (m > 1) {
+    uint64_t n2 = 1;
+    while (n2 < m) n2 <<= 1;
+    uint4* sh = nullptr;
+    uint32_t* sl = nullptr;
+    GG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&sh), 16 * n2, st));
+    GG_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&sl), 4 * n2, st));
+    const int sgrid = sms * 8;
+    gxd::ex_load_kernel<<<sgrid, 256, 0, st>>>(hist_out, label_out, m, n2, sh, sl);
+    for (uint64_t k2 = 2; k2 <= n2; k2 <<= 1)
+      for (uint64_t j = k2 >> 1; j > 0; j >>= 1) gxd::ex_bitonic_kernel<<<sgrid, 256, 0, st>>>(sh, sl, n2, k2, j);
+    gxd::ex_store_kernel<<<sgrid, 256, 0, st>>>(sh, sl, m, hist_out, label_out);
+    const cudaError_t le = cudaGetLastError();
+    GG_CUDA(cudaFreeAsync(sh, st));
+    GG_CUDA(cudaFreeAsync(sl, st));
+    GG_CUDA(le);
+    GG_CUDA(cudaStreamSynchronize(st));
+  }
   return GX_OK;
 }
 

@@ -194,13 +194,27 @@ def test_path_longer_than_the_batch_buffer(cuda):
 
 
 def test_training_and_gradients_are_deterministic(cuda):
-    """Partial gradients per CTA, summed in a fixed order: the same seed gives
-    bit-identical weights, and a gradient does not depend on scheduling."""
+    """Examples sorted by content, partial gradients per CTA summed in a fixed
+    order: exploring, labelling and training twice from scratch gives
+    bit-identical examples and weights, and a gradient does not depend on
+    scheduling."""
     import torch
     nets = [inputs.planted_network(s, n, n_traps=1 + s % 4) for s in range(2) for n in (6, 7)]
     hist, label = guide.collect_examples(nets, MAX_DIST)
+    hist2, label2 = guide.collect_examples(nets, MAX_DIST)
+    assert torch.equal(hist, hist2) and torch.equal(label, label2)
+    # one network's examples ascend as (the 16 histogram bytes as 4 words, label bits)
+    h = gx.load_network(nets[0])
+    o = gx.default_opts(table_bytes=1 << 26, bucket_words=8, group_lanes=1, hash_rounds=32)
+    ws = gx.alloc_workspace(h, o)
+    gx.explore(h, o, ws)
+    h1, l1 = gx.training_set(h, ws, MAX_DIST)
+    words = h1.contiguous().view(torch.int32).view(-1, 4).cpu().numpy().view(np.uint32).astype(np.uint64)
+    bits = l1.cpu().numpy().view(np.uint32).astype(np.uint64)
+    rows = list(zip(*[words[:, c].tolist() for c in range(4)], bits.tolist()))
+    assert len(rows) > 1000 and all(rows[i] <= rows[i + 1] for i in range(len(rows) - 1))
     p1, l1 = guide.train(hist, label, steps=200)
-    p2, l2 = guide.train(hist, label, steps=200)
+    p2, l2 = guide.train(hist2, label2, steps=200)
     assert torch.equal(p1, p2) and torch.equal(l1, l2)
     g1, s1 = gx.mlp_grad(p1, hist, label)
     g2, s2 = gx.mlp_grad(p1, hist, label)
