@@ -276,9 +276,27 @@ __device__ __forceinline__ void push_bin(const GuidedArgs& a, float score, const
   constexpr int E = W + 1;
   int b0 = (int)(score / a.scale * (float)a.nbins);
   b0 = b0 < 0 ? 0 : (b0 >= a.nbins ? a.nbins - 1 : b0);
+  // The calling lanes that share a bin reserve their slots with one atomic
+  // (scores cluster, and same-address atomics serialise in L2).
+  {
+    const uint32_t peers = __match_any_sync(__activemask(), b0);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(&a.bin_count[b0], (unsigned long long)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const unsigned long long pos = base + __popc(peers & ((1u << lane) - 1u));
+    if (pos < a.bin_cap) {
+      uint32_t* e = a.bins + ((uint64_t)b0 * a.bin_cap + pos) * E;
+#pragma unroll
+      for (int w = 0; w < W; ++w) e[w] = v[w];
+      e[W] = parent;
+      return;
+    }
+  }
   // a full bin spills into the next one (cyclically): the bins together hold
   // as many entries as the table has slots, so some bin always has room
-  for (int i = 0; i < a.nbins; ++i) {
+  for (int i = 1; i < a.nbins; ++i) {
     const int b = (b0 + i) % a.nbins;
     const unsigned long long pos = atomicAdd(&a.bin_count[b], 1ull);
     if (pos < a.bin_cap) {
