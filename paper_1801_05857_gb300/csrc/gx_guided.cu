@@ -398,8 +398,13 @@ __global__ void __launch_bounds__(1024) guided_select_kernel(const GuidedArgs a)
 template <int W, int B>
 __global__ void __launch_bounds__(gx::kBlock) guided_expand_kernel(const GuidedArgs a) {
   constexpr int E = W + 1;
+  constexpr int kWarps = gx::kBlock / 32;
+  const unsigned long long n = a.ctl->batch_n;
+  if ((unsigned long long)blockIdx.x * kWarps >= n) return;  // no state for this CTA
   extern __shared__ __align__(16) uint32_t gsm[];
   __shared__ uint64_t muls[kMaxRounds];
+  __shared__ unsigned long long s_sum[3][kWarps];
+  __shared__ uint32_t s_err[kWarps];
   for (int i = threadIdx.x; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
   const uint32_t* t = a.blob;
   if (a.stage) {
@@ -411,18 +416,16 @@ __global__ void __launch_bounds__(gx::kBlock) guided_expand_kernel(const GuidedA
   const NetBlobLayout& L = a.lay;
   const int lane = threadIdx.x & 31;
   const Group<1> g;
-  const unsigned long long n = a.ctl->batch_n;
   const unsigned long long log_base = a.ctl->log_base;
   unsigned long long trans = 0, ins = 0;
   uint32_t probes = 0, err = 0;
   // One warp per state: a batch holds a few thousand states, so the time of an
   // iteration is the latency of one state's successors; lane l takes
-  // successors l, l + 32, ... and their find-or-puts overlap.
-  while (true) {
-    unsigned long long idx = 0;
-    if (lane == 0) idx = atomicAdd(&a.ctl->claim, 1ull);
-    idx = __shfl_sync(FULLMASK, idx, 0);
-    if (idx >= n) break;
+  // successors l, l + 32, ... and their find-or-puts overlap.  Warp w of the
+  // grid takes states w, w + (warps of the grid), ... (no claim counter).
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
+  for (unsigned long long idx = (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5); idx < n;
+       idx += nwarps) {
     uint32_t v[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) v[w] = a.batch[idx * E + w];
@@ -475,15 +478,33 @@ __global__ void __launch_bounds__(gx::kBlock) guided_expand_kernel(const GuidedA
       }
     }
   }
+  // the CTA's totals, one atomic per counter (every warp's at once would queue
+  // on the same addresses)
   trans = warp_sum(trans);
   ins = warp_sum(ins);
   const unsigned long long pr = warp_sum((unsigned long long)probes);
   err = __reduce_or_sync(FULLMASK, err);
+  const int wid = threadIdx.x >> 5;
   if (lane == 0) {
-    if (trans) atomicAdd(&a.ctl->transitions, trans);
-    if (ins) atomicAdd(&a.ctl->inserted, ins);
-    if (pr) atomicAdd(&a.ctl->probes, pr);
-    if (err) atomicOr(&a.ctl->error, err);
+    s_sum[0][wid] = trans;
+    s_sum[1][wid] = ins;
+    s_sum[2][wid] = pr;
+    s_err[wid] = err;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    unsigned long long x = 0;
+    for (int w = 0; w < kWarps; ++w) x += threadIdx.x < 3 ? s_sum[threadIdx.x][w] : (unsigned long long)s_err[w];
+    if (x) {
+      if (threadIdx.x == 0) atomicAdd(&a.ctl->transitions, x);
+      else if (threadIdx.x == 1) atomicAdd(&a.ctl->inserted, x);
+      else if (threadIdx.x == 2) atomicAdd(&a.ctl->probes, x);
+      else {
+        uint32_t e = 0;
+        for (int w = 0; w < kWarps; ++w) e |= s_err[w];
+        atomicOr(&a.ctl->error, e);
+      }
+    }
   }
 }
 
