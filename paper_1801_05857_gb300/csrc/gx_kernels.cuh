@@ -522,13 +522,30 @@ __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expa
     }
   }
   st.flush<W>(tg, err);
+  // the CTA's totals, one atomic per counter: at the end of a level every warp
+  // finishes at once, and per-warp atomics would queue on two addresses
+  __shared__ unsigned long long s_tot[2][gx::kBlock / 32];
+  __shared__ uint32_t s_err[gx::kBlock / 32];
   const unsigned long long trans_w = warp_sum((unsigned long long)trans);
   const unsigned long long pr = warp_sum((unsigned long long)probes);
   err = __reduce_or_sync(FULLMASK, err);
   if (lane == 0) {
-    if (trans_w) atomicAdd(&a.ctl->transitions, trans_w);
-    if (pr) atomicAdd(&a.ctl->probes, pr);
-    if (err) atomicOr(&a.ctl->error, err);
+    s_tot[0][threadIdx.x >> 5] = trans_w;
+    s_tot[1][threadIdx.x >> 5] = pr;
+    s_err[threadIdx.x >> 5] = err;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    unsigned long long x = 0;
+    if (threadIdx.x < 2)
+      for (int w = 0; w < gx::kBlock / 32; ++w) x += s_tot[threadIdx.x][w];
+    if (threadIdx.x == 0 && x) atomicAdd(&a.ctl->transitions, x);
+    if (threadIdx.x == 1 && x) atomicAdd(&a.ctl->probes, x);
+    if (threadIdx.x == 2) {
+      uint32_t e = 0;
+      for (int w = 0; w < gx::kBlock / 32; ++w) e |= s_err[w];
+      if (e) atomicOr(&a.ctl->error, e);
+    }
   }
 }
 
