@@ -64,6 +64,7 @@ MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HI
 
 
 MLP_GRAD_CTAS = 256  # GX_MLP_GRAD_CTAS
+BATCH_WIDE_OFF = 0xFFFFFFFF  # GX_BATCH_WIDE_OFF
 
 
 def mlp_state_bytes(batch: int) -> int:

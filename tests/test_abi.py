@@ -96,3 +96,4 @@ def test_binding_constants_match_the_header():
     assert int(re.search(r"#define GX_MLP_GRAD_CTAS (\d+)", txt).group(1)) == gx.MLP_GRAD_CTAS
     assert int(re.search(r"#define GX_MLP_IN (\d+)", txt).group(1)) == gx.MLP_IN
     assert int(re.search(r"#define GX_MLP_HIDDEN (\d+)", txt).group(1)) == gx.MLP_HIDDEN
+    assert int(re.search(r"#define GX_BATCH_WIDE_OFF (0x[0-9A-Fa-f]+)u", txt).group(1), 16) == gx.BATCH_WIDE_OFF

@@ -48,6 +48,20 @@ def test_mixed_batch_matches_oracle(cuda, bucket, group, chunk):
             _check_net(b, i, r)
 
 
+@pytest.mark.parametrize("wide", [gx.BATCH_WIDE_OFF, 1 << 20])
+def test_lane_and_warp_layouts_alone_match_oracle(cuda, wide):
+    """Every iteration with one state per lane (wide path off), or every iteration with
+    one state per warp and successors by index (a factor no iteration exceeds)."""
+    nets = _mixed()
+    want = [oracle.explore(n) for n in nets]
+    b = gx.batch_create(nets)
+    o = gx.batch_opts(hash_rounds=64, expected_states=[2 * r.states for r in want], wide_factor=wide)
+    ws = gx.batch_alloc_workspace(b, o)
+    gx.batch_explore(b, o, ws)
+    for i, r in enumerate(want):
+        _check_net(b, i, r)
+
+
 def test_autotune_picks_a_working_configuration(cuda):
     nets = _mixed()
     want = [oracle.explore(n) for n in nets]
