@@ -45,7 +45,6 @@ struct GuidedCtl {
   unsigned long long probes;
   unsigned int error, done;
   unsigned long long dl_count;
-  unsigned long long claim;
   unsigned long long pending;    // new states appended by the current iteration's expansion
   unsigned long long iters;      // iterations run
   unsigned long long path_len;   // states on the deadlock's path (gx_guided_trace), 0 if none
@@ -349,7 +348,6 @@ __device__ __forceinline__ bool select_batch(const GuidedArgs& a) {
   if (threadIdx.x == 0) {
     best = 0x7FFFFFFF;
     c.batch_n = 0;
-    c.claim = 0;
     c.pending = 0;
   }
   __syncthreads();
@@ -422,7 +420,7 @@ __global__ void __launch_bounds__(gx::kBlock) guided_expand_kernel(const GuidedA
   // One warp per state: a batch holds a few thousand states, so the time of an
   // iteration is the latency of one state's successors; lane l takes
   // successors l, l + 32, ... and their find-or-puts overlap.  Warp w of the
-  // grid takes states w, w + (warps of the grid), ... (no claim counter).
+  // grid takes states w, w + (warps of the grid), ...
   const unsigned long long nwarps = (unsigned long long)gridDim.x * kWarps;
   for (unsigned long long idx = (unsigned long long)blockIdx.x * kWarps + (threadIdx.x >> 5); idx < n;
        idx += nwarps) {
