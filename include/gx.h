@@ -168,11 +168,12 @@ typedef struct gx_explore_opts {
   uint32_t partition_min_states; /* levels with at least this many states are partitioned;
                                     0 = never (default) */
   uint32_t guided_bins;          /* GX_DL_GUIDED: priority bins; 0 = 32 */
-  uint32_t warp_cache_log2;      /* per-warp cache of recently seen vectors (1- and 2-word
-                                    vectors; the block-local state cache of Fig. 2): 2^n entries
-                                    per warp in shared memory, a hit skips find-or-put.
-                                    0 = off, 0xFFFFFFFF = 2^9; gx_default_opts sets 9
-                                    (mid network: 21 % fewer bucket reads, 8 % faster) */
+  uint32_t warp_cache_log2;      /* per-warp cache of recently seen vectors (the block-local
+                                    state cache of Fig. 2): 2^n entries per warp in shared
+                                    memory (2^(n-1) for 4-word vectors, the same bytes), a hit
+                                    skips find-or-put.  0 = off, 0xFFFFFFFF = 2^9;
+                                    gx_default_opts sets 9 (mid network: 21 % fewer bucket
+                                    reads, 8 % faster) */
   float guided_scale;            /* GX_DL_GUIDED: score at which a state falls in the last
                                     bin (scores are predicted distances / max_dist); 0 = 1.0 */
   uint32_t watch;                /* 1 = safety check (Sec. 3: the negation of a safety property

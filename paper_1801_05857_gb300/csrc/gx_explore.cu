@@ -504,9 +504,10 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   ea.stage = (smem + blob_bytes <= std::min<size_t>(dev.smem_optin, 96 * 1024)) ? 1 : 0;
   if (ea.stage) smem += blob_bytes;
   ea.cache_log2 = 0;
-  if (P.W <= 2 && o->warp_cache_log2) {
+  if (o->warp_cache_log2) {
     ea.cache_log2 = o->warp_cache_log2 == 0xFFFFFFFFu ? 9 : (int)o->warp_cache_log2;
     if (ea.cache_log2 > 12) return fail(GX_ERR_INVALID, "warp_cache_log2 must be at most 12");
+    if (P.W == 4) ea.cache_log2 -= 1;  // 16-byte entries: the same bytes as 2^n 2-word ones
     smem += 4ull * P.W * (kBlock / 32) * (1ull << ea.cache_log2);
     if (smem > dev.smem_optin)
       return fail(GX_ERR_INVALID, "warp cache of 2^" + std::to_string(ea.cache_log2) + " entries per warp needs " +

@@ -357,6 +357,11 @@ struct WarpCache {
       *e = x;
       return false;
     } else {
+      static_assert(W == 4, "slot width");
+      uint4* e = reinterpret_cast<uint4*>(base) + ((uint32_t)h & mask);
+      const uint4 c = *e;
+      if (c.x == v[0] && c.y == v[1] && c.z == v[2] && c.w == v[3]) return true;
+      *e = make_uint4(v[0], v[1], v[2], v[3]);
       return false;
     }
   }
@@ -470,8 +475,8 @@ __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expa
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
   const ParamTarget tg{a, s_range};
   WarpCache cache{nullptr, 0};
-  if (W <= 2 && a.cache_log2 > 0) {
-    uint32_t* cbase = sm + 2 * kMaxRounds + (a.stage ? a.blob_words : 0);
+  if (a.cache_log2 > 0) {
+    uint32_t* cbase = sm + 2 * kMaxRounds + (a.stage ? a.blob_words : 0);  // 16-byte aligned
     const uint32_t per_warp = (1u << a.cache_log2) * W;
     cache.base = cbase + (threadIdx.x >> 5) * per_warp;
     cache.mask = (1u << a.cache_log2) - 1u;
