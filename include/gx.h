@@ -351,6 +351,15 @@ gx_status gx_mlp_init(float* params, uint64_t seed, void* stream);
  * GX_ERR_SPIN_LIMIT if a wait for a tensor-core product timed out. */
 gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, float* out, void* stream);
 
+/* Self-test of failure detection without a GPU fault.  Every wait of the
+ * library's kernels on an mbarrier (the tensor-core products of the scorer)
+ * polls at most a fixed number of times and then reports GX_ERR_SPIN_LIMIT.
+ * This call runs that bounded wait on an mbarrier that nothing arrives on, for
+ * spin_limit polls (1..2^22), in one warp.  It returns GX_ERR_SPIN_LIMIT when
+ * the wait gave up, which is the expected outcome; the context stays usable.
+ * GX_ERR_INVALID for spin_limit 0 or above 2^22.  Synchronises `stream`. */
+gx_status gx_wait_selftest(uint32_t spin_limit, void* stream);
+
 /* Gradient of the mean squared error over n examples at params (grad: device,
  * GX_MLP_PARAMS floats, overwritten; loss: device, one float).  The result
  * does not depend on scheduling (partial gradients summed in a fixed order);

@@ -201,6 +201,19 @@ __global__ void __launch_bounds__(gxt::kRows) mlp_tc_forward_kernel(const gxt::T
   gxt::tc_teardown(sc);
 }
 
+// Self-test of the bounded wait every tensor-core product is awaited with: one
+// warp waits on an mbarrier that nothing arrives on, for `limit` polls, and
+// records that it gave up.
+__device__ unsigned int g_wait_gave_up;
+
+__global__ void wait_selftest_kernel(uint32_t limit) {
+  __shared__ unsigned long long bar;
+  if (threadIdx.x == 0) gxt::mbar_init(gxt::saddr(&bar), 1);
+  __syncthreads();
+  const bool done = gxt::mbar_wait_bounded(gxt::saddr(&bar), 0, limit);
+  if (threadIdx.x == 0) g_wait_gave_up = done ? 0u : 1u;
+}
+
 // Adam (Kingma & Ba 2015) on the FP32 master parameters; clears the gradient.
 __global__ void adam_kernel(float* __restrict__ p, float* __restrict__ m, float* __restrict__ v,
                             float* __restrict__ g, float lr, float b1t, float b2t) {
@@ -307,6 +320,24 @@ gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, f
   GM_CUDA(cudaMemcpyFromSymbolAsync(&err, gxm::g_tc_error, sizeof(err), 0, cudaMemcpyDeviceToHost, st));
   GM_CUDA(cudaStreamSynchronize(st));
   if (err) return gx::fail(GX_ERR_SPIN_LIMIT, "tensor-core scoring timed out waiting for an MMA");
+  return GX_OK;
+}
+
+gx_status gx_wait_selftest(uint32_t spin_limit, void* stream) {
+  gx::clear_error();
+  if (spin_limit == 0 || spin_limit > gxt::kSpinLimit)
+    return gx::fail(GX_ERR_INVALID, "spin_limit must be 1.." + std::to_string(gxt::kSpinLimit));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const unsigned int unset = 2u;
+  GM_CUDA(cudaMemcpyToSymbolAsync(gxm::g_wait_gave_up, &unset, sizeof(unset), 0, cudaMemcpyHostToDevice, st));
+  gxm::wait_selftest_kernel<<<1, 32, 0, st>>>(spin_limit);
+  GM_CUDA(cudaGetLastError());
+  unsigned int gave_up = 2u;
+  GM_CUDA(cudaMemcpyFromSymbolAsync(&gave_up, gxm::g_wait_gave_up, sizeof(gave_up), 0, cudaMemcpyDeviceToHost, st));
+  GM_CUDA(cudaStreamSynchronize(st));
+  if (gave_up == 1u)
+    return gx::fail(GX_ERR_SPIN_LIMIT, "the wait gave up after " + std::to_string(spin_limit) + " polls");
+  if (gave_up != 0u) return gx::fail(GX_ERR_CUDA, "the self-test kernel did not report");
   return GX_OK;
 }
 

@@ -133,6 +133,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "gx_set_digest": ([vp, vp, u64, vp, P(u64), P(u64), P(u64)], ctypes.c_int),
         "gx_find_or_put": ([vp, u64, u32, u32, u32, u32, vp, u64, vp, vp, vp], ctypes.c_int),
         "gx_cuckoo_find_or_put": ([vp, u64, u32, u32, u32, vp, vp, u64, vp, vp, vp], ctypes.c_int),
+        "gx_wait_selftest": ([u32, vp], ctypes.c_int),
         "gx_probe_random": ([u32, vp, u64, u64, u32, u64, vp, vp], ctypes.c_int),
         "gx_explore_noalloc": ([vp, P(gx_explore_opts), vp, P(gx_stats_t), P(u64), u32, P(u32)],
                                ctypes.c_int),
@@ -575,6 +576,11 @@ def cuckoo_find_or_put(keys, key_words: int, table, counters, result=None, n_has
                                        None if m is None else m.ctypes.data, _ptr(table),
                                        table.numel() // key_words, _ptr(result), _ptr(counters),
                                        _stream(stream)))
+
+
+def wait_selftest(spin_limit: int, stream=None) -> None:
+    """gx_wait_selftest: raises GxError(GX_ERR_SPIN_LIMIT) when the bounded wait gave up."""
+    _check(lib().gx_wait_selftest(spin_limit, _stream(stream)))
 
 
 def probe_random(kind: int, buffer, n: int, nbytes: int, seed: int, sink, stream=None) -> None:
