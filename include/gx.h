@@ -334,7 +334,9 @@ gx_status gx_set_digest(gx_net* net, void* workspace, uint64_t workspace_bytes, 
  * uint32 per table slot (gx_stats table_slots).  *n_out = states found (may
  * exceed cap).  The examples come sorted by content (the 16 histogram bytes,
  * then the label's bits, as unsigned words), so with cap >= *n_out the output
- * is the same on every run.  GX_ERR_INVALID if a process has more than 16
+ * is the same on every run; the sort takes 20 bytes of temporary device
+ * memory per example, the count rounded up to a power of two
+ * (cudaMallocAsync on `stream`).  GX_ERR_INVALID if a process has more than 16
  * local states. */
 gx_status gx_training_set(gx_net* net, void* workspace, uint64_t workspace_bytes, void* stream,
                           uint32_t* dist_scratch, uint32_t max_dist, uint8_t* hist_out,
