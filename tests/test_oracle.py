@@ -424,3 +424,21 @@ def test_product_family_closed_forms(seed, n, ns, blocks, parties):
     r = oracle.explore(net)
     assert (r.states, r.transitions, r.deadlock_count) == (S, T, 0)
     assert any(len(rule.parts) == parties for rule in net.rules)
+
+
+def test_planted_networks_have_exactly_the_planted_deadlocks():
+    """The guided-search generator: a global state is a deadlock exactly when every
+    process sits in a trap, so there are n_traps deadlocks (process 0 owns the traps,
+    the others have one).  Each process needs two local moves to reach a trap (into
+    its pre-trap state, which the initial state enters directly, then the fail edge),
+    so the first deadlock is at BFS depth 2n exactly."""
+    for seed in range(3):
+        for n in (3, 4, 5):
+            for k in (1, 2, 3):
+                net = inputs.planted_network(seed, n, n_traps=k)
+                r = oracle.explore(net, deadlocks_cap=64)
+                assert r.deadlock_count == k and r.first_deadlock_level == 2 * n
+                ns0 = net.procs[0].n_states
+                assert sorted(int(d[0]) for d in r.deadlocks) == list(range(ns0 - k, ns0))
+                for d in r.deadlocks:
+                    assert all(int(d[p]) == net.procs[p].n_states - 1 for p in range(1, n))
