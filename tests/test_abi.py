@@ -97,3 +97,19 @@ def test_binding_constants_match_the_header():
     assert int(re.search(r"#define GX_MLP_IN (\d+)", txt).group(1)) == gx.MLP_IN
     assert int(re.search(r"#define GX_MLP_HIDDEN (\d+)", txt).group(1)) == gx.MLP_HIDDEN
     assert int(re.search(r"#define GX_BATCH_WIDE_OFF (0x[0-9A-Fa-f]+)u", txt).group(1), 16) == gx.BATCH_WIDE_OFF
+
+
+def test_limits_at_their_boundaries():
+    LTS, Rule, Network = inputs.LTS, inputs.Rule, inputs.Network
+    # 124 one-bit processes fill four 31-bit words exactly; one more does not fit
+    ok = Network(1, [LTS(2, 0, [(0, 0, 1)]) for _ in range(124)], [])
+    assert gx.layout(gx.load_network(ok))["vector_words"] == 4
+    with pytest.raises(gx.GxError) as e:
+        gx.load_network(Network(1, [LTS(2, 0, [(0, 0, 1)]) for _ in range(125)], []))
+    assert e.value.status == gx.GX_ERR_INVALID and "124" in e.value.message
+    # a rule may have 16 participants, not 17
+    procs = [LTS(2, 0, [(0, 0, 1)]) for _ in range(17)]
+    gx.load_network(Network(1, procs, [Rule([(p, 0) for p in range(16)], 0)]))
+    with pytest.raises(gx.GxError) as e:
+        gx.load_network(Network(1, procs, [Rule([(p, 0) for p in range(17)], 0)]))
+    assert e.value.status == gx.GX_ERR_INVALID and "16" in e.value.message
