@@ -4,15 +4,26 @@ The network (no counterpart in the paper): x = hist / n with n = sum(hist) the
 number of processes (x = 0 for an all-zero row), h1 = relu(W1 x + b1),
 h2 = relu(W2 h1 + b2), y = w3 . h2 + b3, loss = mean (y - label)^2, with the
 parameter vector laid out W1 (128 x 16) | b1 | W2 (128 x 128) | b2 | w3 | b3.
-With bf16=True both factors of every weight product are bfloat16 (the upper
-16 bits of the IEEE binary32 pattern, round to nearest, ties to even), as on
-the tensor cores: the weights W1, W2, w3 are rounded, and so are x (from the
-binary32 product hist * (1 / n), both steps rounded to nearest in binary32)
-and h1 (from its binary32 value) before they enter their layers.
-Everything else is float64.  Gradients are taken with respect to the
-unrounded parameters through the rounded weights and activations (each
-rounding passes gradients unchanged), which is what an optimiser on FP32
-master weights sees.
+Two forms are given.
+
+* ``forward_reference`` is the network as defined: its weights W1, W2, w3
+  are stored as bfloat16 (the parameter vector rounded once, as every kernel
+  reads it), and everything else -- the features x = hist / n, both hidden
+  layers and every sum -- is exact float64.  This is the FP64 reference the
+  tensor-core scores are held to (within 1e-2 of the output's scale,
+  ``output_scale``).
+* ``forward`` / ``loss_and_grad`` with bf16=True are the arithmetic model of
+  the tensor-core kernels, a second and tighter check of where they round.
+  There both factors of every weight product are bfloat16 (the upper 16 bits
+  of the IEEE binary32 pattern, round to nearest, ties to even), as on the
+  tensor cores: the weights W1, W2, w3 are rounded, and so are x (from the
+  binary32 product hist * (1 / n), both steps rounded to nearest in binary32)
+  and h1 (from its binary32 value) before they enter their layers.  Everything
+  else is float64.
+
+Gradients are taken with respect to the unrounded parameters through the
+rounded weights and activations (each rounding passes gradients unchanged),
+which is what an optimiser on FP32 master weights sees.
 """
 import numpy as np
 
@@ -96,3 +107,22 @@ def loss_and_grad(p, hist, label, bf16=True):
     gb1 = d1.sum(axis=0)
     g = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gw3, [gb3]])
     return loss, g
+
+
+def forward_reference(p, hist):
+    """The scoring network by its definition: BF16 weights, float64 for the
+    features (x = hist / n exactly, 0 for an all-zero row), the activations and
+    every sum.  Returns (y, h2) with h2 the second hidden layer."""
+    W1, b1, W2, b2, w3, b3 = _weights(p, True)
+    x = features(hist, bf16=False)
+    h1 = np.maximum(x @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    return h2 @ w3 + b3, h2
+
+
+def output_scale(p, h2):
+    """Magnitude of the terms that sum to each output, sum_j |w3_j| h2_j + |b3|:
+    the denominator of the relative error of a dot product, which stays
+    meaningful when the terms cancel and the output itself is near zero."""
+    _, _, _, _, w3, b3 = _weights(p, True)
+    return np.asarray(h2, dtype=np.float64) @ np.abs(w3) + abs(b3)

@@ -322,6 +322,99 @@ def test_mlp_oracle_features_are_bf16_fractions_of_processes():
     assert y.tolist() == [0.333984375, 0.66796875, 0.25, 1.0, 0.0]
 
 
+def _mlp_params(W1=None, b1=None, W2=None, b2=None, w3=None, b3=0.0):
+    from oracle import mlp
+    H, IN = mlp.H, mlp.IN
+    parts = [np.zeros((H, IN)) if W1 is None else W1, np.zeros(H) if b1 is None else b1,
+             np.zeros((H, H)) if W2 is None else W2, np.zeros(H) if b2 is None else b2,
+             np.zeros(H) if w3 is None else w3, [b3]]
+    return np.concatenate([np.ravel(np.asarray(a, dtype=np.float64)) for a in parts]).astype(np.float32)
+
+
+def test_mlp_reference_features_are_exact_fractions():
+    """Closed form: W1 picks input k into hidden unit 0, W2 and w3 pass unit 0
+    to the output, so y = x_k = hist_k / n exactly in float64 (1/3, 5/7, 2/9),
+    where the kernels' model rounds x to bfloat16 (0.333984375 for 1/3)."""
+    from oracle import mlp
+    for k, row, want in ((0, {0: 1, 1: 2}, 1 / 3), (3, {3: 5, 7: 2}, 5 / 7), (15, {15: 2, 2: 7}, 2 / 9)):
+        W1 = np.zeros((mlp.H, mlp.IN))
+        W1[0, k] = 1.0
+        W2 = np.zeros((mlp.H, mlp.H))
+        W2[0, 0] = 1.0
+        w3 = np.zeros(mlp.H)
+        w3[0] = 1.0
+        h = np.zeros((2, 16), dtype=np.int64)
+        for i, c in row.items():
+            h[0, i] = c
+        y, h2 = mlp.forward_reference(_mlp_params(W1, W2=W2, w3=w3), h)
+        assert y[0] == want and y[1] == 0.0          # an all-zero row has x = 0
+        assert h2[0, 0] == want and (h2[0, 1:] == 0).all()
+
+
+def test_mlp_reference_rounds_weights_only():
+    """Closed form: weights are bfloat16, nothing else.  A weight of 1 + 2^-9
+    (a tie) acts as 1, and 1 + 3 * 2^-9 as 1 + 2^-7 (tie to even), while a bias
+    or a hidden unit of 1 + 2^-9 passes unrounded: with W1 = 0, b1 = 1 + 2^-9,
+    W2[0, 0] = w, w3[0] = 1, y = (1 + 2^-9) w."""
+    from oracle import mlp
+    for w, eff in ((1 + 2 ** -9, 1.0), (1 + 3 * 2 ** -9, 1 + 2 ** -7), (-0.5, -0.5)):
+        W2 = np.zeros((mlp.H, mlp.H))
+        W2[0, 0] = w
+        b1 = np.zeros(mlp.H)
+        b1[0] = 1 + 2 ** -9
+        w3 = np.zeros(mlp.H)
+        w3[0] = 1.0
+        y, _ = mlp.forward_reference(_mlp_params(b1=b1, W2=W2, w3=w3), np.eye(16, dtype=np.int64)[:3])
+        want = max((1 + 2 ** -9) * eff, 0.0)         # the second layer's ReLU
+        assert (y == want).all()
+
+
+def test_mlp_reference_layers_in_order_with_relu_and_biases():
+    """Closed form over all three layers with every unit in use: W1 = c * ones
+    (each hidden unit gets c * sum(x) = c, as the fractions sum to 1) plus b1_j,
+    so h1_j = relu(c + b1_j); W2 = ones / 128 makes every h2 unit the mean of h1
+    plus b2_j, through a ReLU; y = sum_j w3_j h2_j + b3.  Half of the b1 and b2
+    entries are negative enough to be cut by the ReLUs, which a dropped ReLU,
+    a sign error, a transposed W2 (it is not symmetric once row 0 is scaled) or
+    a lost bias would change."""
+    from oracle import mlp
+    H = mlp.H
+    c = 0.5
+    b1 = np.where(np.arange(H) % 2 == 0, 0.25, -1.0)   # even units 0.75, odd units cut to 0
+    W2 = np.full((H, H), 1.0 / H)
+    W2[0] *= 2.0                                        # row 0 (unit 0) doubles its input
+    b2 = np.where(np.arange(H) % 4 == 1, -2.0, 0.125)   # units 1, 5, 9, ... cut to 0
+    w3 = (np.arange(H) - 64) / 64.0                     # multiples of 1/64: exact in bfloat16
+    p = _mlp_params(np.full((H, mlp.IN), c), b1, W2, b2, w3, b3=0.375)
+    h = np.array([[4] + [0] * 14 + [12], [1] * 16], dtype=np.int64)
+    mean_h1 = (H // 2) * 0.75 / H                       # = 0.375
+    h2 = np.array([max((2.0 if j == 0 else 1.0) * mean_h1 + b2[j], 0.0) for j in range(H)])
+    want = float(np.dot(w3, h2) + 0.375)
+    y, got_h2 = mlp.forward_reference(p, h)
+    assert np.allclose(got_h2, h2[None, :], rtol=0, atol=1e-15)
+    assert np.allclose(y, want, rtol=0, atol=1e-14)
+    assert np.allclose(mlp.output_scale(p, got_h2),
+                       np.dot(np.abs(w3), h2) + 0.375, rtol=0, atol=1e-14)
+
+
+def test_mlp_kernel_model_stays_within_the_reference_tolerance():
+    """The kernels' arithmetic model (x and h1 rounded to bfloat16) differs from
+    the reference only by those two roundings, 2^-9 relative each, so on seeded
+    weights and histograms its outputs stay within 1e-2 of the output scale;
+    the largest deviation is a few 1e-3."""
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    H, IN = mlp.H, mlp.IN
+    p = _mlp_params(rng.uniform(-0.25, 0.25, (H, IN)), rng.uniform(-0.1, 0.1, H),
+                    rng.uniform(-H ** -0.5, H ** -0.5, (H, H)), rng.uniform(-0.1, 0.1, H),
+                    rng.uniform(-H ** -0.5, H ** -0.5, H), 0.2)
+    hist = rng.multinomial(14, np.ones(16) / 16, size=4000)
+    y, h2 = mlp.forward_reference(p, hist)
+    dev = np.abs(mlp.forward(p, hist) - y) / mlp.output_scale(p, h2)
+    assert dev.max() < 1e-2
+    assert dev.max() > 1e-5  # the two forms do differ: the model rounds
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_safety_watch_closed_forms_without_rules(seed):
     """Independent processes: the states with process p in local state s are
