@@ -192,6 +192,29 @@ typedef struct gx_explore_opts {
                                     (expand, then a one-thread advance step that records the
                                     level and decides whether to go on); after 4096 levels the
                                     host loop takes over */
+  uint32_t region_passes;        /* passes per BFS level of the direct path, a power of two
+                                    1..16: pass q probes only the successors whose first
+                                    bucket lies in region q of the table (its q-th
+                                    1/region_passes of the buckets); every pass generates
+                                    all successors of the level, the first one counts them.
+                                    One pass's random table reads then stay inside one
+                                    region: on GB300 random reads run at the full rate
+                                    within any 64 GiB and 4x slower across 128 GiB
+                                    (address-translation reach).  Results do not depend on
+                                    it.  0 = auto: the fewest passes whose regions are at
+                                    most 64 GiB (1 for tables up to 64 GiB) */
+  uint32_t global_cache_log2;    /* GPU-wide cache of recently seen vectors (1- and 2-word
+                                    vectors; no effect on 4-word ones): 2^n direct-mapped
+                                    64-bit entries in the workspace, cleared at the start of
+                                    each search and small enough to stay in L2.  A vector
+                                    goes in after its find-or-put found or inserted it, so a
+                                    hit is a known state and skips the table probe; most
+                                    successors of a level lead into the levels just before
+                                    and after it.  0 = off (gx_default_opts), 0xFFFFFFFF =
+                                    2^20, at most 2^26.  Off by default: on the mid network
+                                    2^23 entries cut bucket reads per successor from 0.82 to
+                                    0.30, but the search is bound by successor generation
+                                    there and takes as long (22.4 against 21.5 ms) */
 } gx_explore_opts;
 
 /* Fill *opts with the defaults described above. */
@@ -247,7 +270,7 @@ typedef struct gx_stats_t {
   uint32_t vector_words, slot_words, bucket_words, group_lanes, hash_rounds;
   uint32_t complete;        /* 1 = the search ended because no open state was left */
   uint32_t status;          /* gx_status of the run */
-  uint32_t reserved;
+  uint32_t region_passes;   /* passes per level of the direct path (gx_explore_opts) */
   double fill;              /* states / table_slots */
   double gpu_ms;            /* device time of the search (CUDA events around it) */
   double expand_ms;         /* summed device time of the level-expansion kernels */
@@ -263,6 +286,7 @@ typedef struct gx_stats_t {
   uint64_t kernel_launches; /* kernels the search launched (initialisation, expansion,
                                level-advance steps) */
   uint64_t device_levels;   /* levels expanded by the device-driven loop */
+  uint64_t global_cache_entries; /* entries of the GPU-wide cache used (0 = not used) */
 } gx_stats_t;
 
 /* Copy the statistics of the last search on `net` into *out (host memory).
@@ -459,18 +483,30 @@ gx_status gx_batch_autotune(gx_batch* batch, gx_batch_opts* opts, void* workspac
  * then fails or escapes its accounting), or a latency-critical caller that
  * must not pay cudaFree's device-wide synchronisation.
  *
- * Same search as gx_explore, but all scratch (control block, network tables,
- * frontier ring, hash table) lives in one static device array of
+ * The breadth-first search of gx_explore (levels driven from the host, one
+ * control-block read per level), but all scratch (control block, network
+ * tables, frontier ring, hash table, GPU-wide cache) lives in one static
+ * device array of
  * GX_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads the
  * library holds until the process exits.  No cudaMalloc, cudaFree or other
  * allocating call is made.
- *   - Sizes: table_bytes 0 means 32 MiB; frontier_states as for gx_explore.
- *     If table + frontier + tables exceed the array, GX_ERR_INVALID is
- *     returned with the sizes in the message.
+ *   - Options honoured as by gx_explore: bucket_words, group_lanes,
+ *     hash_rounds, table_bytes (0 means 32 MiB here), frontier_states,
+ *     ctas_per_sm, max_levels, stop_at_first_deadlock, warp_cache_log2 (the
+ *     cache is shared memory only), global_cache_log2 (its entries come from
+ *     the array), region_passes (0 means 1 here), and the safety check
+ *     (watch, watch_proc, watch_state, stop_at_first_violation).
+ *   - Not used: deadlock_cap and violation_cap (deadlocks and violations are
+ *     counted and digested but no state is stored), host_loop (the levels are
+ *     always driven from the host), slice_log2 and successor_buffer (they only
+ *     apply to the partitioned path), and the guided_* fields (BFS only).
+ *   - Rejected with GX_ERR_INVALID: partition_min_states other than 0 (the
+ *     partitioned path needs a successor buffer); sizes for which table +
+ *     frontier + network tables + cache exceed the array (the message gives
+ *     them).
  *   - Outputs: *stats_out (gpu_ms and expand_ms are 0: no events are
  *     created); levels_out receives min(levels_cap, n) level sizes and
- *     *n_levels (may be NULL) the total.  Deadlocks are counted and digested
- *     but not stored.  Nothing is recorded in `net`.
+ *     *n_levels (may be NULL) the total.  Nothing is recorded in `net`.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) and caches it; make that first call before any
  *     stream capture.
@@ -548,6 +584,29 @@ gx_status gx_cuckoo_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t 
  * receives a checksum so the reads cannot be optimised away.  Asynchronous. */
 gx_status gx_probe_random(uint32_t kind, uint32_t* buffer, uint64_t words, uint64_t n,
                           uint32_t bytes, uint64_t seed, uint64_t* sink, void* stream);
+
+/* Random gathers with a chosen launch shape and locality, for measuring the
+ * ceiling the table's random accesses are held against (no counterpart in the
+ * paper).  Over the largest power-of-two number of unit_bytes-sized units (32
+ * or 64) that fits `words` uint32 of `buffer`, `n` accesses at counter-based
+ * pseudo-random unit positions (mix64(seed + i), as gx_probe_random):
+ *   load_bytes:  4 = read one word of the unit (the DRAM still moves the whole
+ *                sector; one register per access in flight), or unit_bytes =
+ *                read the whole unit with 256-bit loads;
+ *   in_flight:   accesses each thread issues before it uses any: 1, 2, 4, 8,
+ *                16, or 32 (4-byte loads only);
+ *   ctas_per_sm: 256-thread CTAs per SM, 1..8, lowered to what the kernel's
+ *                registers allow; *ctas_used (host, may be NULL) gets the
+ *                value launched (the grid is SMs x ctas_used);
+ *   group_log2:  0 = every access independent; g >= log2(unit_bytes) = the
+ *                accesses a warp issues together (32 x in_flight) fall in one
+ *                randomly chosen aligned block of 2^g bytes (page locality).
+ * buffer: device, 256-byte aligned (an offset into a larger allocation
+ * measures one region of it).  sink: device, one uint64 receiving a checksum.
+ * GX_ERR_INVALID for other values.  Asynchronous on `stream`. */
+gx_status gx_probe_gather(uint32_t* buffer, uint64_t words, uint64_t n, uint32_t unit_bytes,
+                          uint32_t load_bytes, uint32_t in_flight, uint32_t ctas_per_sm, uint32_t group_log2,
+                          uint64_t seed, uint64_t* sink, void* stream, uint32_t* ctas_used);
 
 #ifdef __cplusplus
 }

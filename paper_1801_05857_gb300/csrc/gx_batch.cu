@@ -217,6 +217,10 @@ struct SmemTarget {
   __device__ __forceinline__ uint32_t* frontier() const { return w->frontier; }
   __device__ __forceinline__ uint64_t fmask() const { return w->fmask; }
   __device__ __forceinline__ uint64_t begin() const { return w->cur_begin; }
+  __device__ __forceinline__ uint64_t region_mask() const { return 0; }
+  __device__ __forceinline__ uint64_t region_bits() const { return 0; }
+  __device__ __forceinline__ unsigned long long* gcache() const { return nullptr; }
+  __device__ __forceinline__ uint64_t gcache_mask() const { return 0; }
 };
 
 // The batched kernel keeps a network index and chunk bounds besides the

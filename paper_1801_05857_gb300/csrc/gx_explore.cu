@@ -197,6 +197,22 @@ inline int ilog2(uint64_t x) {
   } while (0)
 
 constexpr int kPartCtas = 1024;  // CTAs of the partitioned count/scatter passes (at most)
+// Largest table region one pass of the direct path probes by default: random
+// 32-byte reads run at the full rate over any 64 GiB of a table and 4x slower
+// over 128 GiB (the GPU's address-translation reach).
+constexpr uint64_t kAutoRegionBytes = 64ull << 30;
+
+// Arguments of pass q of `passes` region passes over a table of 2^log2nb buckets.
+inline ExpandArgs region_pass(const ExpandArgs& a, uint32_t passes, uint32_t q) {
+  ExpandArgs r = a;
+  int lp = 0;
+  while ((1u << lp) < passes) ++lp;
+  const int shift = a.log2nb - lp;
+  r.region_mask = passes > 1 ? (uint64_t)(passes - 1) << shift : 0ull;
+  r.region_bits = (uint64_t)q << shift;
+  r.count_states = q == 0 ? 1 : 0;
+  return r;
+}
 
 struct Plan {
   int W = 0, B = 0, G = 0, rounds = 0;
@@ -207,8 +223,10 @@ struct Plan {
   int logp = 0;            // table slices for the partitioned path (0 = path off)
   uint64_t cs = 0;         // successor buffer capacity (vectors)
   uint64_t part_min = 0;   // smallest level that may use the partitioned path
+  uint32_t regions = 1;    // passes per level of the direct path (region passes)
+  uint64_t gcache = 0;     // entries of the GPU-wide cache of seen vectors (0 = off)
   uint64_t off_ctl = 0, off_blob = 0, off_dl = 0, off_viol = 0, off_loop = 0, off_front = 0, off_table = 0;
-  uint64_t off_hist = 0, off_off = 0, off_ptot = 0, off_tot = 0, off_succ = 0;
+  uint64_t off_hist = 0, off_off = 0, off_ptot = 0, off_tot = 0, off_succ = 0, off_gcache = 0;
   uint64_t total = 0;
   const KernelSet* ks = nullptr;
 };
@@ -258,6 +276,22 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
   if ((1ull << P.logp) > P.nb) P.logp = ilog2(P.nb);
   P.part_min = o->partition_min_states;
   if (P.part_min == 0) P.logp = 0;  // path off
+  // region passes: explicit, or the fewest passes whose table regions fit the
+  // GPU's address-translation reach for random accesses (64 GiB measured)
+  if (o->region_passes) {
+    const uint32_t r = o->region_passes;
+    if (r > 16 || (r & (r - 1))) return fail(GX_ERR_INVALID, "region_passes must be a power of two from 1 to 16");
+    P.regions = r;
+  } else {
+    P.regions = 1;
+    while (P.regions < 16 && tbytes / P.regions > kAutoRegionBytes) P.regions *= 2;
+  }
+  if (P.regions > P.nb) P.regions = (uint32_t)P.nb;
+  if (o->global_cache_log2) {
+    const uint32_t k = o->global_cache_log2 == 0xFFFFFFFFu ? 20 : o->global_cache_log2;
+    if (k > 26) return fail(GX_ERR_INVALID, "global_cache_log2 must be at most 26");
+    if (P.W <= 2) P.gcache = 1ull << k;  // 4-word vectors: not used
+  }
   P.cs = o->successor_buffer ? o->successor_buffer : std::min<uint64_t>(slots / 2, (1ull << 32) - 1);
   if (P.logp == 0) P.cs = 0;  // partitioned path off: no buffer
   if (P.cs >= (1ull << 32)) return fail(GX_ERR_INVALID, "successor_buffer must be below 2^32 vectors");
@@ -287,6 +321,8 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
   off = align_up(off + (np ? 4ull * kPartCtas : 0));
   P.off_succ = off;
   off = align_up(off + 4ull * P.W * P.cs);
+  P.off_gcache = off;
+  off = align_up(off + 8ull * P.gcache);
   P.total = off;
   return GX_OK;
 }
@@ -363,6 +399,7 @@ gx_status build_loop_graph(gx_net* h, const Plan& P, Ctl* ctl, uint32_t* table, 
   const uint64_t words = (uint64_t)P.B * P.nb;
   constexpr uint64_t kPiece = 1ull << 30;  // words per memset node
   for (uint64_t w0 = 0; w0 < words; w0 += kPiece) GX_CUDA(add_memset(table + w0, std::min(kPiece, words - w0)));
+  if (eg.gcache) GX_CUDA(add_memset(eg.gcache, 2 * P.gcache));
   auto add_kernel = [&](cudaGraph_t gr, const cudaGraphNode_t* deps, size_t nd, const void* fn, dim3 gd, dim3 bd,
                         size_t sh, void** args, cudaGraphNode_t* out) -> cudaError_t {
     cudaKernelNodeParams kp{};
@@ -374,7 +411,7 @@ gx_status build_loop_graph(gx_net* h, const Plan& P, Ctl* ctl, uint32_t* table, 
     return cudaGraphAddKernelNode(out, gr, deps, nd, &kp);
   };
   InitArgs ia_c = ia;
-  ExpandArgs eg_c = eg;
+  ExpandArgs eg_c = region_pass(eg, P.regions, 0);
   void* args_i[] = {&ia_c};
   void* args_l[] = {&la};
   void* args_e[] = {&eg_c};
@@ -391,6 +428,21 @@ gx_status build_loop_graph(gx_net* h, const Plan& P, Ctl* ctl, uint32_t* table, 
   GX_CUDA(cudaGraphAddNode(&cnode, g, &start, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   GX_CUDA(add_kernel(body, nullptr, 0, P.ks->expand_fn, dim3((unsigned)grid), dim3(kBlock), smem, args_e, &ex));
+  // region passes after the first: clear the claim counter, expand again
+  for (uint32_t q = 1; q < P.regions; ++q) {
+    ExpandArgs eq = region_pass(eg, P.regions, q);
+    void* args_q[] = {&eq};
+    cudaMemsetParams mp{};
+    mp.dst = &ctl->claim;
+    mp.value = 0;
+    mp.elementSize = 4;
+    mp.width = sizeof(ctl->claim) / 4;
+    mp.height = 1;
+    cudaGraphNode_t mz, exq;
+    GX_CUDA(cudaGraphAddMemsetNode(&mz, body, &ex, 1, &mp));
+    GX_CUDA(add_kernel(body, &mz, 1, P.ks->expand_fn, dim3((unsigned)grid), dim3(kBlock), smem, args_q, &exq));
+    ex = exq;
+  }
   GX_CUDA(add_kernel(body, &ex, 1, reinterpret_cast<const void*>(&gxd::level_advance_kernel), dim3(1), dim3(1), 0,
                      args_l, &adv));
   cudaGraphExec_t exec;
@@ -460,9 +512,11 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   // levels on the device unless asked otherwise; the partitioned path needs the host
   const bool device_loop = !o->host_loop && P.logp == 0;
   GX_CUDA(cudaEventRecord(ev0, st));
+  unsigned long long* gcache = P.gcache ? reinterpret_cast<unsigned long long*>(base + P.off_gcache) : nullptr;
   if (!device_loop) {
     GX_CUDA(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
     GX_CUDA(cudaMemsetAsync(table, 0, 4ull * P.B * P.nb, st));
+    if (gcache) GX_CUDA(cudaMemsetAsync(gcache, 0, 8ull * P.gcache, st));
   }
 
   InitArgs ia{};
@@ -488,6 +542,9 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   ea.ctl = ctl;
   ea.dl_buf = dl;
   ea.dl_cap = P.dl_cap;
+  ea.count_states = 1;  // region passes set their own (region_pass)
+  ea.gcache = gcache;
+  ea.gcache_mask = P.gcache ? P.gcache - 1 : 0;
   uint32_t* viol = reinterpret_cast<uint32_t*>(base + P.off_viol);
   if (o->watch) {
     const uint32_t wp = o->watch_proc;
@@ -532,7 +589,7 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   std::vector<uint64_t> lv_probes, lv_trans;
   uint64_t prev_probes = 0, prev_trans = 0;
   bool complete = false, finished = false;
-  uint64_t kernel_launches = device_loop ? 0 : 1, device_levels = 0, d2h_loop = 0;
+  uint64_t kernel_launches = device_loop ? 0 : 1, device_levels = 0, d2h_loop = 0, dev_expand = 0;
   if (device_loop) {
     LoopArgs la{};
     la.ctl = ctl;
@@ -576,9 +633,10 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
     }
     explored = hc->explored;
     levels_done = nd;
-    launches = nd;
+    launches = nd * P.regions;
+    dev_expand = launches;
     device_levels = nd;
-    kernel_launches = 2 + 2 * nd;  // init, start, then expand + advance per level
+    kernel_launches = 2 + (P.regions + 1) * nd;  // init, start, then the passes + advance per level
     first_dl = hc->first_dl;
     first_viol = hc->first_viol;
     complete = hc->complete != 0;
@@ -644,12 +702,14 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
       }
     }
     if (direct) {
-      GX_CUDA(cudaMemsetAsync(&ctl->claim, 0, sizeof(unsigned long long), st));
       const uint64_t warps = (F + 31) / 32;
       const uint64_t want = (warps + kBlock / 32 - 1) / (kBlock / 32);
       const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, max_grid));
-      GX_CUDA(P.ks->expand(ea, grid, smem, st));
-      ++launches;
+      for (uint32_t q = 0; q < P.regions; ++q) {
+        GX_CUDA(cudaMemsetAsync(&ctl->claim, 0, sizeof(unsigned long long), st));
+        GX_CUDA(P.ks->expand(region_pass(ea, P.regions, q), grid, smem, st));
+        ++launches;
+      }
     }
     GX_CUDA(cudaEventRecord(ek1, st));
     GX_CUDA(cudaMemcpyAsync(hc, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
@@ -738,7 +798,9 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   S.gpu_ms = total_ms;
   S.expand_ms = expand_ms;
   S.expand_launches = launches;
-  S.kernel_launches = kernel_launches + (launches - device_levels);
+  S.kernel_launches = kernel_launches + (launches - dev_expand);
+  S.region_passes = P.regions;
+  S.global_cache_entries = P.gcache;
   S.device_levels = device_levels;
   S.probes = hc->probes;
   S.partitioned_levels = part_levels;

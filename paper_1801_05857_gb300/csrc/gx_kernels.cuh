@@ -259,6 +259,10 @@ struct Target {
   __device__ __forceinline__ uint32_t* frontier() const { return front; }
   __device__ __forceinline__ uint64_t fmask() const { return fm; }
   __device__ __forceinline__ uint64_t begin() const { return cur_begin; }
+  __device__ __forceinline__ uint64_t region_mask() const { return 0; }
+  __device__ __forceinline__ uint64_t region_bits() const { return 0; }
+  __device__ __forceinline__ unsigned long long* gcache() const { return nullptr; }
+  __device__ __forceinline__ uint64_t gcache_mask() const { return 0; }
 };
 
 struct ParamTarget {
@@ -271,6 +275,10 @@ struct ParamTarget {
   __device__ __forceinline__ uint32_t* frontier() const { return a.frontier; }
   __device__ __forceinline__ uint64_t fmask() const { return a.fmask; }
   __device__ __forceinline__ uint64_t begin() const { return range[0]; }
+  __device__ __forceinline__ uint64_t region_mask() const { return a.region_mask; }
+  __device__ __forceinline__ uint64_t region_bits() const { return a.region_bits; }
+  __device__ __forceinline__ unsigned long long* gcache() const { return a.gcache; }
+  __device__ __forceinline__ uint64_t gcache_mask() const { return a.gcache_mask; }
 };
 
 // Per-warp staging of new vectors in shared memory: lanes that inserted a
@@ -367,6 +375,29 @@ struct WarpCache {
   }
 };
 
+// GPU-wide cache of recently seen vectors: direct-mapped, 2^k 64-bit entries in
+// global memory (a few MB, so it stays in L2), cleared at the start of a search.
+// A vector is written into it after its find-or-put found or inserted it, so
+// every entry is a vector of the table and a hit can skip the table probe.
+// Only 1- and 2-word vectors: an aligned 64-bit load or store is one access, so
+// an entry is never seen half-written.  Successors of a level mostly lead into
+// the levels just before and after it, which were inserted or looked up
+// moments earlier by some warp of the GPU.
+template <int W>
+__device__ __forceinline__ unsigned long long gcache_key(const uint32_t (&v)[W]) {
+  if constexpr (W == 1) return (unsigned long long)v[0];
+  else return (unsigned long long)v[0] | ((unsigned long long)v[W > 1 ? 1 : 0] << 32);
+}
+template <int W>
+__device__ __forceinline__ bool gcache_hit(const unsigned long long* c, uint64_t mask, uint64_t h,
+                                           const uint32_t (&v)[W]) {
+  return __ldcg(c + ((h >> 32) & mask)) == gcache_key<W>(v);
+}
+template <int W>
+__device__ __forceinline__ void gcache_put(unsigned long long* c, uint64_t mask, uint64_t h, const uint32_t (&v)[W]) {
+  __stcg(c + ((h >> 32) & mask), gcache_key<W>(v));
+}
+
 // Successors each lane generates per round.  insert_lanes takes K per lane
 // (the group issues the first-bucket loads of up to four items before it
 // resolves any of them); measured on the mid network, K = 2 or 4 costs more in
@@ -408,13 +439,19 @@ __device__ __forceinline__ void insert_lanes(const T& a, const uint64_t* muls,
       for (int w = 0; w < W; ++w) x[j][w] = g.template bcast<uint32_t>(s[i % K][w], src);
       if (hv[j]) {
         const uint64_t hh = vec_hash<W>(x[j]);
+        const uint64_t b = bucket_of(hh, muls[0], a.log2nb());
+        // region passes: a vector whose first bucket lies outside this pass's region is
+        // left to the pass of that region (tested before the cache, which may only hold
+        // vectors that went to find-or-put)
+        if ((b & a.region_mask()) != a.region_bits()) hv[j] = false;
         // a vector this warp has already sent to find-or-put needs no second lookup
-        if (cache.base && cache.template seen<W>(hh, x[j])) hv[j] = false;
-      }
-      if (hv[j]) {
-        const uint64_t b = bucket_of(vec_hash<W>(x[j]), muls[0], a.log2nb());
-        load_words<LW>(a.table() + b * (uint64_t)B + (uint64_t)g.glane * LW, pre[j]);
-        probes += g.glane == 0;
+        else if (cache.base && cache.template seen<W>(hh, x[j])) hv[j] = false;
+        // nor does one that any warp found or inserted moments ago
+        else if (W <= 2 && a.gcache() && gcache_hit<W>(a.gcache(), a.gcache_mask(), hh, x[j])) hv[j] = false;
+        if (hv[j]) {
+          load_words<LW>(a.table() + b * (uint64_t)B + (uint64_t)g.glane * LW, pre[j]);
+          probes += g.glane == 0;
+        }
       }
     }
 #pragma unroll
@@ -424,6 +461,8 @@ __device__ __forceinline__ void insert_lanes(const T& a, const uint64_t* muls,
       const int r = find_or_put_from<W, B, G, true>(a.table(), a.log2nb(), a.rounds(), muls, x[j], g, probes,
                                                     pre[j]);
       if (r == FOP_FULL) err |= gx::ERR_TABLE_FULL;
+      else if (W <= 2 && a.gcache() && g.glane == 0)
+        gcache_put<W>(a.gcache(), a.gcache_mask(), vec_hash<W>(x[j]), x[j]);
       if (g.glane == i / K && r == FOP_INSERTED) inserted[i % K] = true;
     }
   }
@@ -497,15 +536,17 @@ __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expa
     for (int w = 0; w < W; ++w) v[w] = 0;
     if (valid) load_vec<W>(a.frontier + (idx & a.fmask) * W, v);
     uint32_t remaining = valid ? count_succ<W>(t, L, v) : 0u;
-    trans += remaining;
-    if (valid && remaining == 0) {
+    // with region passes, the level's states are accounted for in the first pass only
+    const bool acct = valid && a.count_states;
+    if (acct) trans += remaining;
+    if (acct && remaining == 0) {
       const uint64_t h = state_digest<W>(t, L, v);
       const unsigned long long di = atomicAdd(&a.ctl->dl_count, 1ull);
       atomicAdd(&a.ctl->dl_sum, (unsigned long long)h);
       atomicXor(&a.ctl->dl_xor, (unsigned long long)h);
       if (di < a.dl_cap) store_vec<W>(a.dl_buf + di * W, v);
     }
-    if (a.watch && valid) check_watch<W>(a, t, L, v);
+    if (a.watch && acct) check_watch<W>(a, t, L, v);
     SuccIter it;
     it.init();
     constexpr int K = PerLane<G>::K;

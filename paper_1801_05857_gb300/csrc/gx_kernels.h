@@ -63,6 +63,16 @@ struct ExpandArgs {
   uint32_t* viol_buf;        // violating vectors, W words each
   uint32_t viol_cap;
   int dev_range;             // 1: read cur_begin / cur_end from the control block
+  // Region passes: a level is expanded in several passes, and a pass probes only
+  // the successors whose first bucket b has (b & region_mask) == region_bits, so
+  // the table accesses of one pass stay inside one region of the table (see
+  // gx_explore_opts.region_passes).  region_mask = 0: one pass, no filter.
+  uint64_t region_mask, region_bits;
+  int count_states;          // 1: this pass counts transitions, deadlocks and violations
+  // GPU-wide cache of recently seen vectors (1- and 2-word vectors): 2^k entries of
+  // 64 bits in global memory, small enough to stay in L2; nullptr = off
+  unsigned long long* gcache;
+  uint64_t gcache_mask;
 };
 
 // Partitioned expansion of one level (or one batch of it): successors are

@@ -37,6 +37,42 @@ probe_gather_kernel(const uint32_t* __restrict__ buf, uint64_t unit_mask, uint64
   if ((threadIdx.x & 31) == 0 && acc) atomicXor(sink, (unsigned long long)acc);
 }
 
+// Gathers with a chosen launch shape and access locality, for measuring the
+// random-access ceiling itself.  Access i reads LW words at the start of unit
+// u(i) of UNIT_WORDS words (LW = 1 touches one word, which still moves the
+// whole sector, with one register per access in flight).  Each thread issues
+// K accesses before it uses any.  With group_bits = g > 0, the 32 x K accesses
+// of one warp iteration fall in one randomly chosen aligned block of 2^g
+// units (locality within a page), otherwise every access is independent.
+template <int K, int LW>
+__global__ void __launch_bounds__(gx::kBlock)
+probe_sweep_kernel(const uint32_t* __restrict__ buf, int unit_words, uint64_t unit_mask, uint32_t group_bits,
+                   uint64_t n, uint64_t seed, unsigned long long* sink) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x * K;
+  const uint64_t inner = (1ull << group_bits) - 1ull;
+  uint32_t acc = 0;
+  for (uint64_t i0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) * K; i0 < n; i0 += stride) {
+    // i0 / (32 K) is the same in every lane of the warp (the stride is a multiple of 32 K)
+    const uint64_t block = group_bits ? (mix64(~seed ^ (i0 / (32ull * K))) & unit_mask & ~inner) : 0ull;
+    // every position is inside the buffer, so all K loads are issued without a
+    // branch; those past n are simply not used
+    uint32_t x[K][LW];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+      const uint64_t r = mix64(seed + i0 + j);
+      const uint64_t u = group_bits ? (block | (r & inner)) : (r & unit_mask);
+      load_words<LW>(buf + u * (uint64_t)unit_words, x[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      if (i0 + j < n)
+#pragma unroll
+        for (int w = 0; w < LW; ++w) acc ^= x[j][w];
+  }
+  acc = __reduce_xor_sync(FULLMASK, acc);
+  if ((threadIdx.x & 31) == 0 && acc) atomicXor(sink, (unsigned long long)acc);
+}
+
 __global__ void __launch_bounds__(gx::kBlock)
 probe_cas_kernel(uint32_t* __restrict__ buf, uint64_t unit_mask, int unit_words, uint64_t n,
                  uint64_t seed, unsigned long long* sink) {
@@ -311,6 +347,57 @@ gx_status gx_probe_random(uint32_t kind, uint32_t* buffer, uint64_t words, uint6
     gxd::probe_cas_kernel<<<grid, gx::kBlock, 0, st>>>(buffer, n_units - 1, unit_words, n, seed,
                                                        reinterpret_cast<unsigned long long*>(sink));
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
+  return GX_OK;
+}
+
+gx_status gx_probe_gather(uint32_t* buffer, uint64_t words, uint64_t n, uint32_t unit_bytes,
+                          uint32_t load_bytes, uint32_t in_flight, uint32_t ctas_per_sm, uint32_t group_log2,
+                          uint64_t seed, uint64_t* sink, void* stream, uint32_t* ctas_used) {
+  gx::clear_error();
+  if (!buffer || !sink) return gx::fail(GX_ERR_INVALID, "NULL device pointer");
+  if (reinterpret_cast<uintptr_t>(buffer) % 256) return gx::fail(GX_ERR_INVALID, "buffer is not 256-byte aligned");
+  if (unit_bytes != 32 && unit_bytes != 64) return gx::fail(GX_ERR_INVALID, "unit_bytes must be 32 or 64");
+  if (load_bytes != 4 && load_bytes != unit_bytes)
+    return gx::fail(GX_ERR_INVALID, "load_bytes must be 4 or unit_bytes");
+  const int K = (int)in_flight;
+  if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32)
+    return gx::fail(GX_ERR_INVALID, "in_flight must be 1, 2, 4, 8, 16 or 32");
+  if (load_bytes > 4 && K > 16) return gx::fail(GX_ERR_INVALID, "in_flight above 16 only with 4-byte loads");
+  if (ctas_per_sm < 1 || ctas_per_sm > 8) return gx::fail(GX_ERR_INVALID, "ctas_per_sm must be 1..8");
+  const int unit_words = (int)unit_bytes / 4;
+  if ((uint64_t)unit_words > words) return gx::fail(GX_ERR_INVALID, "buffer smaller than one access");
+  uint64_t n_units = 1;
+  while (n_units * 2 * unit_words <= words) n_units *= 2;
+  uint32_t gbits = 0;
+  if (group_log2) {
+    uint32_t ub = unit_bytes == 32 ? 5 : 6;
+    if (group_log2 < ub) return gx::fail(GX_ERR_INVALID, "group_log2 smaller than one unit");
+    gbits = group_log2 - ub;
+    if ((1ull << gbits) > n_units) return gx::fail(GX_ERR_INVALID, "locality group larger than the buffer");
+  }
+  const void* fn = nullptr;
+  using Fn = void (*)(const uint32_t*, int, uint64_t, uint32_t, uint64_t, uint64_t, unsigned long long*);
+  Fn f = nullptr;
+  const int lw = (int)load_bytes / 4;
+#define GX_SWEEP(KK, LL) \
+  if (K == KK && lw == LL) f = gxd::probe_sweep_kernel<KK, LL>;
+  GX_SWEEP(1, 1) GX_SWEEP(2, 1) GX_SWEEP(4, 1) GX_SWEEP(8, 1) GX_SWEEP(16, 1) GX_SWEEP(32, 1)
+  GX_SWEEP(1, 8) GX_SWEEP(2, 8) GX_SWEEP(4, 8) GX_SWEEP(8, 8) GX_SWEEP(16, 8)
+  GX_SWEEP(1, 16) GX_SWEEP(2, 16) GX_SWEEP(4, 16) GX_SWEEP(8, 16) GX_SWEEP(16, 16)
+#undef GX_SWEEP
+  if (!f) return gx::fail(GX_ERR_INVALID, "no such probe shape");
+  fn = reinterpret_cast<const void*>(f);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, gx::kBlock, 0);
+  if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
+  const int ctas = (int)ctas_per_sm < per_sm ? (int)ctas_per_sm : (per_sm > 0 ? per_sm : 1);
+  if (ctas_used) *ctas_used = (uint32_t)ctas;
+  if (n == 0) return GX_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  f<<<sm_count() * ctas, gx::kBlock, 0, st>>>(buffer, unit_words, n_units - 1, gbits, n, seed,
+                                               reinterpret_cast<unsigned long long*>(sink));
+  e = cudaGetLastError();
   if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
   return GX_OK;
 }

@@ -56,7 +56,7 @@ class gx_explore_opts(ctypes.Structure):
                 ("partition_min_states", u32), ("guided_bins", u32), ("warp_cache_log2", u32),
                 ("guided_scale", ctypes.c_float), ("watch", u32), ("watch_proc", u32),
                 ("watch_state", u32), ("stop_at_first_violation", u32), ("violation_cap", u32),
-                ("host_loop", u32)]
+                ("host_loop", u32), ("region_passes", u32), ("global_cache_log2", u32)]
 
 
 MLP_IN, MLP_HIDDEN = 16, 128
@@ -78,12 +78,12 @@ class gx_stats_t(ctypes.Structure):
                 ("first_deadlock_level", i64), ("table_slots", u64),
                 ("vector_words", u32), ("slot_words", u32), ("bucket_words", u32),
                 ("group_lanes", u32), ("hash_rounds", u32), ("complete", u32), ("status", u32),
-                ("reserved", u32), ("fill", ctypes.c_double), ("gpu_ms", ctypes.c_double),
+                ("region_passes", u32), ("fill", ctypes.c_double), ("gpu_ms", ctypes.c_double),
                 ("expand_ms", ctypes.c_double), ("expand_launches", u64), ("probes", u64),
                 ("h2d_bytes", u64), ("d2h_bytes", u64), ("partitioned_levels", u64),
                 ("violation_count", u64), ("violation_sum", u64), ("violation_xor", u64),
                 ("first_violation_level", ctypes.c_int64), ("kernel_launches", u64),
-                ("device_levels", u64)]
+                ("device_levels", u64), ("global_cache_entries", u64)]
 
 
 class gx_batch_opts(ctypes.Structure):
@@ -135,6 +135,7 @@ def lib(build_if_missing: bool = True) -> ctypes.CDLL:
         "gx_cuckoo_find_or_put": ([vp, u64, u32, u32, u32, vp, vp, u64, vp, vp, vp], ctypes.c_int),
         "gx_wait_selftest": ([u32, vp], ctypes.c_int),
         "gx_probe_random": ([u32, vp, u64, u64, u32, u64, vp, vp], ctypes.c_int),
+        "gx_probe_gather": ([vp, u64, u64, u32, u32, u32, u32, u32, u64, vp, vp, P(u32)], ctypes.c_int),
         "gx_explore_noalloc": ([vp, P(gx_explore_opts), vp, P(gx_stats_t), P(u64), u32, P(u32)],
                                ctypes.c_int),
         "gx_training_set": ([vp, vp, u64, vp, vp, u32, vp, vp, u64, P(u64)], ctypes.c_int),
@@ -339,7 +340,7 @@ def find_deadlocks(net: Net, mode: int, opts: gx_explore_opts | None = None, wor
 def stats(net: Net) -> dict:
     s = gx_stats_t()
     _check(lib().gx_stats(net.handle, ctypes.byref(s)))
-    return {name: getattr(s, name) for name, _ in gx_stats_t._fields_ if name != "reserved"}
+    return {name: getattr(s, name) for name, _ in gx_stats_t._fields_ }
 
 
 def levels(net: Net) -> list:
@@ -395,7 +396,7 @@ def explore_noalloc(net: Net, opts: gx_explore_opts | None = None, stream=None,
     _check(lib().gx_explore_noalloc(net.handle, ctypes.byref(opts) if opts else None,
                                     _stream(stream), ctypes.byref(s), lv.ctypes.data_as(P(u64)),
                                     levels_cap, ctypes.byref(n)))
-    stats_d = {name: getattr(s, name) for name, _ in gx_stats_t._fields_ if name != "reserved"}
+    stats_d = {name: getattr(s, name) for name, _ in gx_stats_t._fields_ }
     return stats_d, [int(x) for x in lv[:min(int(n.value), levels_cap)]]
 
 
@@ -530,7 +531,7 @@ def batch_explore(b: Batch, opts: gx_batch_opts | None, workspace, stream=None) 
 def batch_stats(b: Batch, i: int) -> dict:
     s = gx_stats_t()
     _check(lib().gx_batch_stats(b.handle, i, ctypes.byref(s)))
-    return {name: getattr(s, name) for name, _ in gx_stats_t._fields_ if name != "reserved"}
+    return {name: getattr(s, name) for name, _ in gx_stats_t._fields_ }
 
 
 def batch_levels(b: Batch, i: int) -> list:
@@ -586,3 +587,14 @@ def wait_selftest(spin_limit: int, stream=None) -> None:
 def probe_random(kind: int, buffer, n: int, nbytes: int, seed: int, sink, stream=None) -> None:
     _check(lib().gx_probe_random(kind, _ptr(buffer), buffer.numel(), n, nbytes, seed, _ptr(sink),
                                  _stream(stream)))
+
+
+def probe_gather(buffer, n: int, unit_bytes: int, load_bytes: int, in_flight: int, ctas_per_sm: int,
+                 group_log2: int, seed: int, sink, stream=None) -> int:
+    """Random gathers over `buffer` (an int32 device tensor, or a slice of one) with the given
+    launch shape and locality; returns the CTAs per SM launched."""
+    used = ctypes.c_uint32(0)
+    _check(lib().gx_probe_gather(_ptr(buffer), buffer.numel(), n, unit_bytes, load_bytes, in_flight,
+                                 ctas_per_sm, group_log2, seed, _ptr(sink), _stream(stream),
+                                 ctypes.byref(used)))
+    return used.value

@@ -350,3 +350,87 @@ def test_product_family_against_closed_forms(cuda, seed, n, ns, blocks):
     else:
         _, s, _, _ = run_gpu(net, table_bytes=1 << 30, bucket_words=32, hash_rounds=32)
     assert (s["states"], s["transitions"], s["deadlock_count"], s["complete"]) == (S, T, 0, 1)
+
+
+@pytest.mark.parametrize("passes", [2, 4, 16])
+@pytest.mark.parametrize("host_loop", [1, 0])
+@pytest.mark.parametrize("net", [inputs.token_ring(11), inputs.workload("tiny"),
+                                 inputs.random_network(0, 13, 64, 1, 3, 16, n_sync=8, parties=3, cluster=4),
+                                 inputs.random_network(6, 8, 8, 0, 2, 10, n_sync=4, parties=2)],
+                         ids=lambda n: n.name)
+def test_region_passes_are_exact(cuda, net, passes, host_loop):
+    """Region passes (each level expanded once per table region, a pass probing only
+    the successors whose first bucket is in its region) give the oracle's results
+    bit for bit: counts, levels, deadlock and set digests, in both level loops."""
+    s = assert_parity(net, table_bytes=1 << 25, region_passes=passes, host_loop=host_loop)
+    assert s["region_passes"] == passes
+    assert s["expand_launches"] == passes * (s["n_levels"])
+
+
+def test_region_passes_with_full_buckets_and_the_safety_check(cuda):
+    """At high fill a vector's later hash rounds leave its region; the safety check
+    and the transition count are taken in the first pass only."""
+    net = inputs.token_ring(9)
+    r = oracle.explore(net, watch=(3, 4))
+    h = gx.load_network(net)
+    o = gx.default_opts(table_bytes=1 << 19, hash_rounds=64, bucket_words=4, region_passes=8,
+                        watch=1, watch_proc=3, watch_state=4)
+    gx.explore(h, o, gx.alloc_workspace(h, o))
+    s = gx.stats(h)
+    assert s["fill"] > 0.8
+    assert (s["states"], s["transitions"], gx.levels(h)) == (r.states, r.transitions, r.levels)
+    assert (s["violation_count"], s["violation_sum"], s["violation_xor"], s["first_violation_level"]) == \
+        (r.violation_count, r.violation_sum, r.violation_xor, r.first_violation_level)
+
+
+def test_region_passes_are_validated(cuda):
+    h = gx.load_network(inputs.token_ring(5))
+    for bad in (3, 32):
+        with pytest.raises(gx.GxError) as e:
+            gx.explore(h, gx.default_opts(table_bytes=1 << 20, region_passes=bad), None)
+        assert e.value.status == gx.GX_ERR_INVALID
+    o = gx.default_opts(table_bytes=1 << 20)
+    gx.explore(h, o, None)
+    assert gx.stats(h)["region_passes"] == 1  # auto: tables up to 64 GiB take one pass
+
+
+@pytest.mark.parametrize("log2", [0, 4, 12, 20])
+@pytest.mark.parametrize("host_loop", [1, 0])
+@pytest.mark.parametrize("net", [inputs.token_ring(11), inputs.workload("tiny"),
+                                 inputs.random_network(1, 10, 16, 1, 3, 12, n_sync=4, parties=2, cluster=4),
+                                 inputs.random_network(6, 8, 8, 0, 2, 10, n_sync=4, parties=2)],
+                         ids=lambda n: n.name)
+def test_global_cache_keeps_results_exact(cuda, net, log2, host_loop):
+    """The GPU-wide cache of seen vectors (2^0 entries: every vector fights for one;
+    2^20: the default) only skips probes of vectors already in the table, so the
+    results equal the oracle's; with it on, fewer buckets are read."""
+    s = assert_parity(net, table_bytes=1 << 25, global_cache_log2=log2, host_loop=host_loop, warp_cache_log2=0)
+    assert s["global_cache_entries"] == (1 << log2 if log2 else 0)
+
+
+def test_global_cache_reads_fewer_buckets_and_ignores_4_word_vectors(cuda):
+    net = inputs.random_network(1, 10, 16, 1, 3, 12, n_sync=4, parties=2, cluster=4)
+    base = assert_parity(net, table_bytes=1 << 25, global_cache_log2=0, warp_cache_log2=0)
+    with_cache = assert_parity(net, table_bytes=1 << 25, global_cache_log2=20, warp_cache_log2=0)
+    assert with_cache["probes"] < 0.8 * base["probes"]
+    s4 = assert_parity(inputs.random_network(0, 13, 64, 1, 3, 16, n_sync=8, parties=3, cluster=4),
+                       table_bytes=1 << 25, global_cache_log2=20)
+    assert s4["slot_words"] == 4 and s4["global_cache_entries"] == 0
+
+
+def test_global_cache_is_cleared_between_searches(cuda):
+    """Two different networks explored one after the other in the same workspace:
+    entries left by the first are not hits in the second."""
+    import torch
+    a = inputs.random_network(1, 10, 16, 1, 3, 12, n_sync=4, parties=2, cluster=4)
+    b = inputs.random_network(2, 10, 16, 1, 3, 12, n_sync=4, parties=2, cluster=4)
+    o = gx.default_opts(table_bytes=1 << 25, global_cache_log2=16)
+    ha, hb = gx.load_network(a), gx.load_network(b)
+    ws = gx.alloc_workspace(ha, o)
+    assert gx.workspace_bytes(hb, o) <= ws.numel()
+    for h, net in ((ha, a), (hb, b), (ha, a)):
+        gx.explore(h, o, ws)
+        torch.cuda.synchronize()
+        r = oracle.explore(net)
+        s = gx.stats(h)
+        assert (s["states"], s["transitions"], gx.levels(h)) == (r.states, r.transitions, r.levels)

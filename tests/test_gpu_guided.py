@@ -81,9 +81,45 @@ def test_tensor_core_forward_tiles_match_float64(cuda, n):
         hist_np[1, 0] = 16
     y = gx.mlp_forward(p, torch.from_numpy(hist_np).cuda()).cpu().numpy()
     pick = np.unique(np.concatenate([np.arange(min(n, 300)), rng.integers(0, n, 700), [n - 1]]))
-    yr = omlp.forward(p.cpu().numpy(), hist_np[pick])
     assert np.isfinite(y).all()
-    assert np.max(np.abs(y[pick] - yr)) < 1e-4
+    _check_scores(p.cpu().numpy(), hist_np[pick], y[pick])
+
+
+def _check_scores(pn, hist_np, y):
+    """Scores against the FP64 reference (the network's definition: BF16 weights,
+    float64 features, activations and sums) within 1e-2 of each output's scale
+    (sum_j |w3_j| h2_j + |b3|), element by element; and against the kernels'
+    arithmetic model (x and h1 also rounded to BF16) within 1e-4 absolute, the
+    tighter check of where they round."""
+    yr, h2 = omlp.forward_reference(pn, hist_np)
+    rel = np.abs(y - yr) / omlp.output_scale(pn, h2)
+    assert rel.max() <= 1e-2, (rel.argmax(), y[rel.argmax()], yr[rel.argmax()])
+    assert np.max(np.abs(y - omlp.forward(pn, hist_np))) < 1e-4
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 4099, 152 * 4 * 128 * 2 + 77])
+def test_trained_scores_match_float64_reference(cuda, trained_params, n):
+    """The same tile sizes with a trained guide, whose outputs are distance
+    estimates in [0, 1] rather than near-zero sums of cancelling terms: every
+    score is also within 1e-2 of the reference relative to the score itself
+    wherever the score is at least 0.05 in size."""
+    import torch
+    rng = np.random.default_rng(100 + n)
+    k = rng.integers(6, 17, size=n)
+    hist_np = np.stack([np.bincount(rng.integers(0, 16, kk), minlength=16) for kk in k]).astype(np.uint8)
+    y = gx.mlp_forward(trained_params, torch.from_numpy(hist_np).cuda()).cpu().numpy()
+    pn = trained_params.cpu().numpy()
+    _check_scores(pn, hist_np, y)
+    yr, _ = omlp.forward_reference(pn, hist_np)
+    big = np.abs(yr) >= 0.05
+    assert big.any() or n == 1
+    assert np.max(np.abs(y[big] - yr[big]) / np.abs(yr[big])) <= 1e-2
+
+
+@pytest.fixture(scope="module")
+def trained_params(cuda):
+    params, _ = _trained(600)
+    return params
 
 
 def _trained(steps=600):
