@@ -37,11 +37,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mid")
-    ap.add_argument("--bucket", type=int, default=8)
-    ap.add_argument("--group", type=int, default=1)
-    ap.add_argument("--rounds", type=int, default=32)
-    ap.add_argument("--table-log2-words", type=int, default=28)
+    ap.add_argument("--workload", default="scaled",
+                    help="scaled (the memory-scaled configuration, 128 GiB table), scaled90, mid or tiny")
+    ap.add_argument("--bucket", type=int, default=0, help="bucket words (0 = the workload's setting)")
+    ap.add_argument("--group", type=int, default=0, help="lanes per bucket (0 = the workload's setting)")
+    ap.add_argument("--rounds", type=int, default=0, help="hash rounds (0 = the workload's setting)")
+    ap.add_argument("--table-log2-words", type=int, default=0,
+                    help="log2 of the table's words (0 = the workload's setting)")
     ap.add_argument("--slice-log2", type=int, default=0)
     ap.add_argument("--nodes", type=int, default=19, help="token-ring nodes for --experiment scaled")
     ap.add_argument("--family", default="ring", choices=["ring", "product"],
@@ -51,6 +53,11 @@ def parse():
     ap.add_argument("--level-loop", default="host", choices=["host", "device"],
                     help="main line: levels driven by the host (profilable kernel by kernel) or by "
                          "the device (one CUDA graph); the other one is timed beside it")
+    ap.add_argument("--global-cache", type=int, default=0,
+                    help="log2 entries of the GPU-wide cache of seen vectors (0 = off)")
+    ap.add_argument("--region-passes", type=int, default=0,
+                    help="passes per level, each probing one region of the table (0 = auto: regions "
+                         "of at most 64 GiB)")
     ap.add_argument("--partition-min", type=int, default=0,
                     help="partition levels with at least this many states (0 = never)")
     ap.add_argument("--cpu-sample", type=int, default=3_000_000,
@@ -61,14 +68,30 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided deadlock-search part")
     ap.add_argument("--experiment", default="", choices=["", "table-sweep", "cuckoo-sweep", "bucket-sweep", "scaled", "scaling-table", "scorer", "batch",
-                             "guided"],
+                             "guided", "cache-sweep"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
                          "exploration for every (bucket, group) size; scaled: one large token ring; "
                          "scaling-table: ring and producer/consumer families by size (Table 1); "
                          "scorer: the tensor-core scoring kernel alone; batch: the 256-network batch "
                          "alone; guided: one guided search with a host round trip per iteration; "
+                         "cache-sweep: --workload for per-warp and GPU-wide cache sizes; "
                          "one JSON line per point")
-    return ap.parse_args()
+    args = ap.parse_args()
+    wl = WORKLOAD_SETTINGS.get(args.workload, WORKLOAD_SETTINGS["mid"])
+    for k in ("bucket", "group", "rounds", "table_log2_words"):
+        if not getattr(args, k):
+            setattr(args, k, wl[k])
+    return args
+
+
+# Table settings per workload: log2 of the table's uint32 words, bucket words, lanes per
+# bucket, hash rounds.  The memory-scaled network fills 62.5 % of a 128 GiB table.
+WORKLOAD_SETTINGS = {
+    "scaled": dict(table_log2_words=35, bucket=16, group=1, rounds=64),
+    "scaled90": dict(table_log2_words=35, bucket=32, group=1, rounds=64),
+    "mid": dict(table_log2_words=28, bucket=8, group=1, rounds=32),
+    "tiny": dict(table_log2_words=16, bucket=32, group=1, rounds=8),
+}
 
 
 def dist_setup():
@@ -178,20 +201,35 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": mx, "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def ncu_traffic(args) -> dict | None:
-    """DRAM bytes of the expansion kernel from the committed ncu capture, when it was taken
-    on this workload and configuration and the kernel sources have not changed since."""
+def ncu_traffic(args, s: dict, probes: int, launches: int) -> dict | None:
+    """DRAM bytes per launch of the expansion kernel from a committed one-kernel ncu
+    capture (profiles/expand_kernel_<workload>_traffic.json), used when it was taken on
+    this workload's configuration and the kernel sources have not changed since.  A
+    capture of a smaller table than this run's (the size rule for counter captures) is
+    scaled by algorithmic bytes: its DRAM bytes per algorithmic byte times this run's
+    algorithmic bytes per launch."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "expand_kernel_mid_traffic.json")
-    if not os.path.exists(path) or args.workload != "mid" or (args.bucket, args.group) != (8, 1) \
-            or args.table_log2_words != 28 or args.warp_cache != 9:
+    path = os.path.join(ROOT, "profiles", f"expand_kernel_{args.workload}_traffic.json")
+    if not os.path.exists(path):
         return None
     with open(path) as f:
         t = json.load(f)
+    cfg = t.get("config", {})
+    if (cfg.get("bucket"), cfg.get("group"), cfg.get("warp_cache")) != (args.bucket, args.group, args.warp_cache):
+        return None
     src = b"".join(open(os.path.join(ROOT, p), "rb").read() for p in t["kernel_sources"])
     if hashlib.sha256(src).hexdigest() != t["kernel_sources_sha256"]:
         return None
-    return t
+    if cfg.get("table_log2_words") == args.table_log2_words and cfg.get("region_passes", 1) == s["region_passes"]:
+        return {"dram_bytes_per_launch": int(t["dram_bytes_per_search"] // max(launches, 1)),
+                "source": f"profiles/{os.path.basename(path)}: ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                          "of the same configuration, per launch"}
+    ratio = t["dram_bytes_per_search"] / t["algorithmic_bytes_per_search"]
+    alg = algorithmic_bytes(dict(s, probes=probes))
+    return {"dram_bytes_per_launch": int(ratio * alg / max(launches, 1)),
+            "source": f"profiles/{os.path.basename(path)}: ncu dram__bytes_read.sum + dram__bytes_write.sum "
+                      f"on a {cfg.get('table_gib')} GiB table, {ratio:.3f} DRAM bytes per algorithmic byte, "
+                      "scaled to this run's algorithmic bytes per launch"}
 
 
 def algorithmic_bytes(s: dict) -> int:
@@ -226,6 +264,45 @@ def random_access_peak(torch, gx) -> dict:
         # a CAS moves one 32-byte sector in and out of DRAM at best
         out[name + "_gbs"] = round(n * (nbytes if kind == 0 else 32) / sec / 1e9, 1)
     del buf
+    return out
+
+
+def random_access_ceiling(torch, gx, ws, s: dict) -> dict:
+    """Random 32-byte read rates of this table size, over the search's own workspace
+    (read only, after the timed searches): independent reads over the largest
+    power-of-two span of it (the table's span), and reads confined to one region of
+    that span as a region pass issues them.  The ceiling of the probes is the rate of
+    the reads the kernel actually issues."""
+    buf = ws.view(torch.int32)
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.cuda.current_stream()
+    n = 1 << 28
+    out = {}
+    span = 1
+    while span * 2 <= buf.numel():
+        span *= 2
+    table_words = s["table_slots"] * s["slot_words"]
+    regions = s["region_passes"]
+
+    def rate(b, seed):
+        gx.probe_gather(b, n, 32, 32, 4, 8, 0, seed, sink)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for k in range(3):
+            gx.probe_gather(b, n, 32, 32, 4, 8, 0, seed + 1 + k, sink)
+        e1.record(st)
+        torch.cuda.synchronize()
+        return n / (e0.elapsed_time(e1) / 3 * 1e-3) / 1e9
+
+    span_t = min(span, 1 << (table_words.bit_length() - 1))
+    out["independent_g_per_s"] = round(rate(buf[:span_t], 101), 3)
+    out["span_gib"] = round(4 * span_t / 2 ** 30, 2)
+    region_words = span_t // regions
+    out["region_gib"] = round(4 * region_words / 2 ** 30, 2)
+    out["in_region_g_per_s"] = round(rate(buf[:region_words], 201), 3) if regions > 1 else out["independent_g_per_s"]
+    out["ceiling_g_per_s"] = out["in_region_g_per_s"]
+    out["note"] = ("32-byte reads, 4 in flight per thread, 8 CTAs of 256 threads per SM; the rate is the same "
+                   "at every depth and occupancy measured (profiles/random_access_roofline.md)")
     return out
 
 
@@ -392,22 +469,26 @@ def guided_part(torch, gx, inputs, guide) -> dict:
             del ws
             torch.cuda.empty_cache()
 
-    def bfs(net):
+    def bfs(net, table_gib):
         h = gx.load_network(net)
-        o = gx.default_opts(table_bytes=24 << 30, hash_rounds=32, frontier_states=1 << 30)
+        o = gx.default_opts(table_bytes=table_gib << 30, hash_rounds=32,
+                            frontier_states=1 << (30 if table_gib <= 24 else 32))
         ws = gx.alloc_workspace(h, o)
         try:
             n, _ = gx.find_deadlocks(h, gx.GX_DL_BFS_FIRST, o, ws)
             s = gx.stats(h)
             return {"found": n, "explored": s["explored"], "stored": s["states"], "ms": round(s["gpu_ms"], 3),
-                    "first_deadlock_level": s["first_deadlock_level"]}
+                    "first_deadlock_level": s["first_deadlock_level"], "table_gib": table_gib,
+                    "fill": round(s["fill"], 4)}
         except gx.GxError as e:
-            return {"error": STATUS(e)}
+            s = gx.stats(h)
+            return {"error": STATUS(e), "table_gib": table_gib, "stored": s["states"],
+                    "levels_done": s["n_levels"], "ms": round(s["gpu_ms"], 3)}
         finally:
             del ws
             torch.cuda.empty_cache()
 
-    # five seeds per size; BFS where its table fits (at 16 processes it does not in 24 GiB)
+    # five seeds per size; BFS in a 24 GiB table up to 14 processes and a 128 GiB one at 16
     rows, summary = [], []
     for n, k in ((12, 2), (13, 2), (14, 2), (16, 3)):
         per = []
@@ -417,7 +498,7 @@ def guided_part(torch, gx, inputs, guide) -> dict:
             # five runs per seed; the untrained guide and BFS once
             runs = [guided(net, params) for _ in range(5)]
             per.append({"network": net.name, "guided_runs": runs, "untrained": guided(net, untrained),
-                        "bfs": bfs(net) if n <= 14 else {"skipped": "table beyond 24 GiB"}})
+                        "bfs": bfs(net, 24 if n <= 14 else 128)})
         rows.extend(per)
 
         def med(vals):
@@ -472,10 +553,37 @@ def STATUS(e) -> str:
     return str(e).split(":")[0]
 
 
+def host_cpu() -> dict:
+    """The host's CPU model and logical core count (the oracle's single thread runs on one)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.TimeoutExpired):
+            pass
+    import platform
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count(),
+            "machine": platform.machine()}
+
+
 def cpu_baseline(net, sample: int) -> dict:
     import oracle
     r = oracle.explore(net, max_explored=sample)
     return {"value": round(r.states / r.seconds, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": f"first {len(r.levels)} BFS levels of the same network ({r.explored} states "
                       f"explored, {r.states} found) in {r.seconds:.1f} s, single thread, "
                       f"std::unordered_set"}
@@ -502,12 +610,73 @@ def run_reference(args, world, rank, pg):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * wall / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload} network {inputs.WORKLOADS[args.workload]}"},
-            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "config": {"workload": f"{args.workload}: {net.name} {inputs.workload_params(args.workload)}"},
+            "cpu_baseline": {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                              "sample": f"each step: BFS of the {args.workload} network until {sample} "
                                        f"states explored, single thread"},
             "e2e": {"value": round(v, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def search_opts(gx, args, host_loop: bool, table_log2_words: int | None = None):
+    return gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
+                           table_bytes=4 << (table_log2_words or args.table_log2_words),
+                           slice_log2=args.slice_log2, partition_min_states=args.partition_min,
+                           warp_cache_log2=args.warp_cache, region_passes=args.region_passes,
+                           global_cache_log2=args.global_cache, host_loop=int(host_loop))
+
+
+def time_searches(torch, gx, h, opts, ws, steps: int) -> dict:
+    """`steps` complete searches back to back, timed with CUDA events on the launching
+    stream; the per-search counters summed over them."""
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    acc = dict(expand_ms=0.0, expand_launches=0, probes=0, kernel_launches=0)
+    e0.record(st)
+    for _ in range(steps):
+        gx.explore(h, opts, ws)
+        si = gx.stats(h)
+        for k in acc:
+            acc[k] += si[k]
+    e1.record(st)
+    torch.cuda.synchronize()
+    acc["ms"] = e0.elapsed_time(e1)
+    acc["last"] = gx.stats(h)
+    return acc
+
+
+def expected_counts(name: str, net):
+    """Closed-form states and transitions of a product workload, else None."""
+    from paper_1801_05857_gb300 import inputs
+    if name in inputs.PRODUCT_WORKLOADS:
+        return product_closed_form(net, inputs.PRODUCT_WORKLOADS[name]["blocks"])
+    return None
+
+
+def roofline_of(s: dict, t: dict, steps: int, peaks: dict) -> dict:
+    """Roofline of the level-expansion kernel over `steps` timed searches."""
+    s_avg = dict(s)
+    s_avg["probes"] = t["probes"] // steps
+    bytes_per_search = algorithmic_bytes(s_avg)
+    launches = t["expand_launches"] // steps
+    # the expansion kernels' time per search: the CUDA events around the timed searches
+    # on their stream (the launch list gives them > 99 % of a search), so the rate is a
+    # slight underestimate
+    ms_search = t["ms"] / steps
+    achieved = bytes_per_search / (ms_search * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, sequential copy)",
+            "kernel": "expand_kernel", "launches_per_step": launches,
+            "avg_launch_ms": round(ms_search / max(launches, 1), 4),
+            "avg_launch_ms_source": "CUDA events around the timed searches on the launching stream / "
+                                    "expansion launches",
+            "level_timer_ms_per_step": round(t["expand_ms"] / steps, 3),
+            "algorithmic_bytes_per_step": bytes_per_search,
+            "algorithmic_bytes_per_launch": bytes_per_search // max(launches, 1),
+            "probes_per_successor": round(s_avg["probes"] / max(s["transitions"], 1), 4),
+            "probes_per_s": round(s_avg["probes"] / (ms_search * 1e-3) / 1e9, 3),
+            "region_passes": s["region_passes"]}
 
 
 def run_ours(args, world, rank, local, pg):
@@ -515,19 +684,15 @@ def run_ours(args, world, rank, local, pg):
     from paper_1801_05857_gb300 import gx, inputs
 
     torch.cuda.set_device(local)
+    peaks = measured_peaks()
     net = inputs.workload(args.workload)
+    want = expected_counts(args.workload, net)
     h = gx.load_network(net)
-    table_bytes = 4 << args.table_log2_words
-    opts = gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
-                           table_bytes=table_bytes, slice_log2=args.slice_log2,
-                           partition_min_states=args.partition_min, warp_cache_log2=args.warp_cache,
-                           host_loop=int(args.level_loop == "host"))
+    opts = search_opts(gx, args, host_loop=args.level_loop == "host")
     ws = gx.alloc_workspace(h, opts)
-    st = torch.cuda.current_stream()
 
     for _ in range(max(args.warmup, 0)):
         gx.explore(h, opts, ws)
-    s = gx.stats(h)
     lv = gx.levels(h)
 
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
@@ -535,95 +700,89 @@ def run_ours(args, world, rank, local, pg):
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    expand_ms, launches, probes, kernels = 0.0, 0, 0, 0
-    for _ in range(args.steps):
-        gx.explore(h, opts, ws)
-        si = gx.stats(h)
-        expand_ms += si["expand_ms"]
-        launches += si["expand_launches"]
-        probes += si["probes"]
-        kernels += si["kernel_launches"]
-    e1.record(st)
-    torch.cuda.synchronize()
+    t = time_searches(torch, gx, h, opts, ws, args.steps)
     barrier(pg)
     clocks = sampler.stop() if sampler else None
-    ms = e0.elapsed_time(e1)
+    ms = t["ms"]
     ms_max = max_over_ranks(ms, pg)
-    s = gx.stats(h)
+    s = t["last"]
     states, trans = s["states"], s["transitions"]
+    exact = None
+    if want is not None:
+        exact = {"states_closed_form": want[0], "transitions_closed_form": want[1],
+                 "equal": states == want[0] and trans == want[1]}
+        if not exact["equal"]:
+            print(json.dumps({"error": "closed-form mismatch", "states": states, "transitions": trans,
+                              **exact}), flush=True)
+            sys.exit(1)
     value = replica_throughput(states * args.steps, ms * 1e-3, pg)
     tps = replica_throughput(trans * args.steps, ms * 1e-3, pg)
+    roof = roofline_of(s, t, args.steps, peaks)
+    tr = ncu_traffic(args, s, t["probes"] // args.steps, t["expand_launches"] // args.steps)
+    roof["traffic"] = tr["dram_bytes_per_launch"] if tr else None
+    roof["traffic_source"] = tr["source"] if tr else "no capture for this kernel and configuration"
 
-    # roofline of the dominant kernel (level expansion)
-    peaks = measured_peaks()
-    s_avg = dict(s)
-    s_avg["probes"] = probes // args.steps
-    bytes_per_search = algorithmic_bytes(s_avg)
-    # the expansion kernel's time per step from the CUDA events around the timed
-    # region on its stream: the whole step (99.98 % of it is that kernel in the
-    # launch list), so the rate is a slight underestimate
-    exp_ms_per_search = ms / args.steps
-    achieved = bytes_per_search / (exp_ms_per_search * 1e-3) / 1e9
-    tr = ncu_traffic(args)
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": round(achieved / peaks["hbm_gbs"], 4),
-            "traffic": tr["dram_bytes_per_launch"] if tr else None,
-            "traffic_source": "profiles/expand_kernel_mid_traffic.json (ncu dram__bytes_read.sum + "
-                              "dram__bytes_write.sum, bytes per launch)" if tr else "no capture for this kernel",
-            "algorithmic_bytes_per_launch": bytes_per_search // max(launches // args.steps, 1),
-            "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs, sequential copy)",
-            "kernel": "expand_kernel", "launches_per_step": launches // args.steps,
-            "avg_launch_ms": round(ms / max(launches, 1), 4),
-            "avg_launch_ms_source": "CUDA events around the timed steps on the launching stream / expansion launches",
-            "level_timer_ms_per_step": round(expand_ms / args.steps, 3),
-            "algorithmic_bytes_per_step": bytes_per_search,
-            "probes_per_successor": round(s_avg["probes"] / max(trans, 1), 4)}
-    if rank == 0:
-        rp = random_access_peak(torch, gx)
-        roof["random_access"] = {k: (round(v / 1e9, 3) if k.endswith("_per_s") else v)
-                                 for k, v in rp.items()}
-        roof["random_access_unit"] = "G accesses/s, GB/s"
-        roof["probes_per_s"] = round(s_avg["probes"] / (exp_ms_per_search * 1e-3) / 1e9, 3)
-        # the bucket reads are random 32-byte accesses: their ceiling is the measured
-        # random-gather rate of the same box, not the sequential copy peak
-        roof["frac_of_random_gather32"] = round(roof["probes_per_s"] / roof["random_access"]["gather32_per_s"], 4)
-
-    # the other level loop on the same workload and workspace, timed the same way
     other = None
     if rank == 0:
-        alt = gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
-                              table_bytes=table_bytes, slice_log2=args.slice_log2,
-                              partition_min_states=args.partition_min, warp_cache_log2=args.warp_cache,
-                              host_loop=int(args.level_loop != "host"))
-        for _ in range(2):
-            gx.explore(h, alt, ws)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(st)
-        for _ in range(args.steps):
-            gx.explore(h, alt, ws)
-        a1.record(st)
-        torch.cuda.synchronize()
-        am = a0.elapsed_time(a1) / args.steps
-        sa = gx.stats(h)
+        # the random-access ceiling of this table size, measured over the search's own
+        # workspace (read only): independent random reads, and reads within one region
+        # of the table as a region pass issues them
+        roof["random_access"] = random_access_ceiling(torch, gx, ws, s)
+        roof["probes_per_s_ceiling"] = roof["random_access"]["ceiling_g_per_s"]
+        roof["frac_of_random_gather32"] = round(roof["probes_per_s"] / roof["random_access"]["ceiling_g_per_s"], 4)
+        # the other level loop on the same workload and workspace
+        alt = search_opts(gx, args, host_loop=args.level_loop != "host")
+        gx.explore(h, alt, ws)
+        ta = time_searches(torch, gx, h, alt, ws, 1 if want is not None else min(args.steps, 5))
+        sa = ta["last"]
+        am = ta["ms"] / max(1, (1 if want is not None else min(args.steps, 5)))
         other = {"level_loop": "host" if args.level_loop != "host" else "device (CUDA graph, conditional WHILE node)",
                  "ms_per_step": round(am, 3), "states_per_s": round(sa["states"] / (am * 1e-3), 1),
                  "kernel_launches_per_step": sa["kernel_launches"]}
 
+    # end to end through the public API with host-resident inputs: load the network from
+    # host arrays, search (on the same caller-owned workspace), read the statistics and
+    # level sizes back to the host
+    e2e = None
+    if not args.no_e2e:
+        flat = net.flat()
+        k = min(args.steps, 3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(k):
+            h2 = gx.load_network(flat)
+            gx.explore(h2, opts, ws)
+            s2 = gx.stats(h2)
+            gx.levels(h2)
+            h2d += s2["h2d_bytes"]
+            d2h += s2["d2h_bytes"] + 8 * s2["n_levels"]
+            del h2
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e2e = {"value": round(replica_throughput(states * k, wall, pg), 1), "unit": UNIT,
+               "h2d_bytes_per_step": h2d // k, "d2h_bytes_per_step": d2h // k, "steps": k}
+    del ws
+    torch.cuda.empty_cache()
+
+    mid = None
+    if rank == 0 and args.workload != "mid":
+        mid = mid_part(torch, gx, inputs, args, peaks)
+
     # Sec. 5.1: 10^8 one-word keys into a 2^27-word table (74.5 % fill at duplication 1)
-    table_part = None
     if rank == 0 and not args.no_table:
         n = 100_000_000
-        g32 = roof.get("random_access", {}).get("gather32_per_s")
-        g32 = g32 * 1e9 if g32 else None
+        rp = random_access_peak(torch, gx)
+        g32 = rp["gather32_per_s"]
         pts = []
         for dup, bucket, group in ((1, 16, 2), (21, 8, 2)):
             nd = n - n % dup
             keys = table_keys(torch, nd, dup)
             pts.append(table_point(torch, gx, keys, nd, dup, 1, 1 << 27, bucket, group, 32, g32))
             del keys
-        table_part = {"keys": n, "key_words": 1, "table_words": 1 << 27, "points": pts}
+        roof["find_or_put"] = {"keys": n, "key_words": 1, "table_words": 1 << 27,
+                               "random_gather32_g_per_s_4gib": round(g32 / 1e9, 3), "points": pts,
+                               "target": ">= 0.5 of the random-gather rate at <= 75 % fill (d = 1)"}
 
     batch_part = None
     if rank == 0 and not args.no_batch:
@@ -632,28 +791,6 @@ def run_ours(args, world, rank, local, pg):
     if rank == 0 and not args.no_guided:
         from paper_1801_05857_gb300 import guide
         guided_res = guided_part(torch, gx, inputs, guide)
-
-    # end to end through the public API with host-resident inputs: load the network
-    # description from host arrays, explore with a library-allocated workspace, read the
-    # results back to the host
-    e2e = None
-    if not args.no_e2e:
-        flat = net.flat()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        h2d = d2h = 0
-        for _ in range(args.steps):
-            h2 = gx.load_network(flat)
-            gx.explore(h2, opts, None)
-            s2 = gx.stats(h2)
-            gx.levels(h2)
-            h2d += s2["h2d_bytes"]
-            d2h += s2["d2h_bytes"] + 8 * s2["n_levels"]
-            del h2
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - t0
-        e2e = {"value": round(replica_throughput(states * args.steps, wall, pg), 1), "unit": UNIT,
-               "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -665,27 +802,67 @@ def run_ours(args, world, rank, local, pg):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
-            "config": {"workload": f"{args.workload} network {inputs.WORKLOADS[args.workload]}",
+            "config": {"workload": f"{args.workload}: {net.name} {inputs.workload_params(args.workload)}",
                        "states": states, "transitions": trans, "levels": len(lv),
-                       "vector_words": s["vector_words"], "bucket_words": s["bucket_words"],
-                       "group_lanes": s["group_lanes"], "hash_rounds": s["hash_rounds"],
-                       "table_words": 1 << args.table_log2_words, "fill": round(s["fill"], 4),
-                       "partitioned_levels": s["partitioned_levels"],
-                       "l2": "1 GiB table > 129 MB L2 (no flush needed)",
+                       "fan_in": round(trans / max(states, 1), 2),
+                       "vector_words": s["vector_words"], "slot_words": s["slot_words"],
+                       "bucket_words": s["bucket_words"], "group_lanes": s["group_lanes"],
+                       "hash_rounds": s["hash_rounds"], "table_words": 1 << args.table_log2_words,
+                       "table_gib": round(4 * (1 << args.table_log2_words) / 2 ** 30, 2),
+                       "fill": round(s["fill"], 4), "region_passes": s["region_passes"],
+                       "partitioned_levels": s["partitioned_levels"], "exact": exact,
+                       "l2": f"{round(4 * (1 << args.table_log2_words) / 2 ** 30, 2)} GiB table > 129 MB L2 "
+                             "(no flush needed)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "transitions_per_s": round(tps, 1),
             "roofline": roof,
-            "find_or_put": table_part,
+            "mid_network": mid,
             "batched": batch_part,
             "guided_deadlock_search": guided_res,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": kernels,
+            "gpu_launches": t["kernel_launches"],
             "level_loop": "device (CUDA graph, conditional WHILE node)" if s["device_levels"] else "host",
             "other_level_loop": other,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
+
+
+def mid_part(torch, gx, inputs, args, peaks, steps: int = 10) -> dict:
+    """The mid network (10 x 16 states, 2-word vectors, 1 GiB table), the paper-sized
+    configuration, timed the same way as the main line."""
+    class A:
+        pass
+    a = A()
+    for k, v in vars(args).items():
+        setattr(a, k, v)
+    a.workload = "mid"
+    for k, v in WORKLOAD_SETTINGS["mid"].items():
+        setattr(a, k, v)
+    a.region_passes = 0
+    net = inputs.workload("mid")
+    h = gx.load_network(net)
+    o = search_opts(gx, a, host_loop=True)
+    ws = gx.alloc_workspace(h, o)
+    for _ in range(3):
+        gx.explore(h, o, ws)
+    t = time_searches(torch, gx, h, o, ws, steps)
+    s = t["last"]
+    roof = roofline_of(s, t, steps, peaks)
+    tr = ncu_traffic(a, s, t["probes"] // steps, t["expand_launches"] // steps)
+    roof["traffic"] = tr["dram_bytes_per_launch"] if tr else None
+    od = search_opts(gx, a, host_loop=False)
+    gx.explore(h, od, ws)
+    td = time_searches(torch, gx, h, od, ws, steps)
+    del ws
+    torch.cuda.empty_cache()
+    ms = t["ms"] / steps
+    return {"workload": f"mid: {net.name} {inputs.WORKLOADS['mid']}", "states": s["states"],
+            "transitions": s["transitions"], "levels": s["n_levels"], "fill": round(s["fill"], 4),
+            "steps": steps, "ms_per_step": round(ms, 3), "states_per_s": round(s["states"] / (ms * 1e-3), 1),
+            "transitions_per_s": round(s["transitions"] / (ms * 1e-3), 1),
+            "device_loop_ms_per_step": round(td["ms"] / steps, 3), "roofline": roof}
 
 
 def product_closed_form(net, blocks):
@@ -712,20 +889,19 @@ def product_closed_form(net, blocks):
     return S, T
 
 
-# the memory-scaled product network: 20 processes x 16 local states (4-word slots),
-# 3-party rules on 10 % of 30 labels, reachable blocks 3^18 * 4 * 5 = 7.75e9 states
-PRODUCT_SCALED = dict(seed=7, n_procs=20, n_states=16, blocks=[3] * 18 + [4, 5])
 
 
 def scaled_experiment(torch, gx, inputs, args):
     """Memory-scaled exploration in a table of 2^--table-log2-words words; one line per
     level with the table fill after it, then a summary binned by fill.  --family ring:
     the token ring with --nodes nodes (2N 3^(N-1) states, 4 N^2 3^(N-2) transitions);
-    --family product: inputs.product_network(**PRODUCT_SCALED) (closed forms above)."""
+    --family product: the product workload --workload names (scaled or scaled90; closed
+    forms above)."""
     n = args.nodes
     if args.family == "product":
-        net = inputs.product_network(**PRODUCT_SCALED)
-        want_states, want_trans = product_closed_form(net, PRODUCT_SCALED["blocks"])
+        name = args.workload if args.workload in inputs.PRODUCT_WORKLOADS else "scaled90"
+        net = inputs.workload(name)
+        want_states, want_trans = product_closed_form(net, inputs.PRODUCT_WORKLOADS[name]["blocks"])
     else:
         net = inputs.token_ring(n)
         want_states = 2 * n * 3 ** (n - 1)
@@ -733,7 +909,8 @@ def scaled_experiment(torch, gx, inputs, args):
     h = gx.load_network(net)
     o = gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
                         table_bytes=4 << args.table_log2_words, slice_log2=args.slice_log2,
-                        partition_min_states=args.partition_min, warp_cache_log2=args.warp_cache)
+                        partition_min_states=args.partition_min, warp_cache_log2=args.warp_cache,
+                        region_passes=args.region_passes, global_cache_log2=args.global_cache)
     ws = gx.alloc_workspace(h, o)
     gx.explore(h, o, ws)
     s = gx.stats(h)
@@ -765,6 +942,7 @@ def scaled_experiment(torch, gx, inputs, args):
                "table_gib": round(4 * s["table_slots"] * W / 2 ** 30, 1), "fill": round(s["fill"], 4),
                "bucket_words": s["bucket_words"], "group_lanes": s["group_lanes"], "gpu_ms": round(s["gpu_ms"], 1),
                "partitioned_levels": s["partitioned_levels"], "slice_log2": args.slice_log2,
+               "region_passes": s["region_passes"],
                "states_per_s": round(s["states"] / (s["gpu_ms"] * 1e-3), 1),
                "by_fill_decile": {f"{10 * b}-{10 * b + 10}%": {"new_states": v[0], "ms": round(v[1], 1),
                                                               "states_per_s": round(v[0] / (v[1] * 1e-3), 1) if v[1] else None,
@@ -890,6 +1068,31 @@ def run_experiment(args):
         scaling_table(torch, gx, inputs, args)
     elif args.experiment == "scaled":
         scaled_experiment(torch, gx, inputs, args)
+    elif args.experiment == "cache-sweep":
+        # per-warp cache x GPU-wide cache sizes on --workload (device level loop), median of
+        # --steps searches after --warmup
+        net = inputs.workload(args.workload)
+        h = gx.load_network(net)
+        ws = None
+        for wc in (0, 9):
+            for gc in (0, 14, 16, 18, 20, 22, 23):
+                o = search_opts(gx, args, host_loop=False)
+                o.warp_cache_log2 = wc
+                o.global_cache_log2 = gc
+                if ws is None:
+                    o2 = search_opts(gx, args, host_loop=False)
+                    o2.global_cache_log2 = 26
+                    ws = gx.alloc_workspace(h, o2)
+                ts = []
+                for _ in range(args.warmup + args.steps):
+                    gx.explore(h, o, ws)
+                    ts.append(gx.stats(h)["gpu_ms"])
+                ts = sorted(ts[args.warmup:])
+                s = gx.stats(h)
+                print(json.dumps({"experiment": "cache-sweep", "workload": args.workload, "warp_cache_log2": wc,
+                                  "global_cache_log2": gc, "ms_median": round(ts[len(ts) // 2], 3),
+                                  "states": s["states"], "states_per_s": round(s["states"] / (ts[len(ts) // 2] * 1e-3), 1),
+                                  "probes_per_successor": round(s["probes"] / s["transitions"], 4)}), flush=True)
     elif args.experiment == "bucket-sweep":
         net = inputs.workload(args.workload)
         h = gx.load_network(net)

@@ -379,8 +379,28 @@ WORKLOADS = {
 }
 
 
+# Memory-scaled workloads: product networks (every combination of block states is
+# reachable, so states and transitions are closed forms at any size).
+PRODUCT_WORKLOADS = {
+    # 16 processes x 16 local states (4 bits each: 3 words, padded to 4-word slots),
+    # 3-party rules on 3 of 30 labels (10 %), out-degree 1-2 inside blocks of 4 local
+    # states (one of 5): 4^15 * 5 = 5.37e9 states, 62.5 % of a 2^33-slot (128 GiB) table
+    "scaled": dict(seed=7, n_procs=16, n_states=16, blocks=[4] * 15 + [5], deg_lo=1, deg_hi=2,
+                   name="scaled_s7_n16"),
+    # the same family taken to 90 % fill: 20 processes, out-degree 1-3, blocks of 3
+    # (one of 4, one of 5): 7.75e9 states in 2^33 slots
+    "scaled90": dict(seed=7, n_procs=20, n_states=16, blocks=[3] * 18 + [4, 5], name="scaled90_s7_n20"),
+}
+
+
 def workload(name: str) -> Network:
+    if name in PRODUCT_WORKLOADS:
+        return product_network(**PRODUCT_WORKLOADS[name])
     return random_network(**WORKLOADS[name])
+
+
+def workload_params(name: str) -> dict:
+    return dict(PRODUCT_WORKLOADS[name]) if name in PRODUCT_WORKLOADS else dict(WORKLOADS[name])
 
 
 def batch_params(seed: int) -> dict:

@@ -21,8 +21,9 @@ def test_reference_arm_prints_the_contract_line():
               "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert k in d, k
     assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 1 and d["value"] > 0
-    assert d["higher_is_better"] is True and d["config"]["workload"].startswith("mid network")
+    assert d["higher_is_better"] is True and d["config"]["workload"].startswith("scaled:")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["host"]["nproc"] >= 1 and cb["host"]["cpu_model"]
     e = d["e2e"]
     assert (e["value"], e["unit"], e["h2d_bytes_per_step"], e["d2h_bytes_per_step"]) == (d["value"], d["unit"], 0, 0)
