@@ -1,6 +1,7 @@
 """Write the stored oracle results used by the GPU parity tests and the bench.
 
     python tests/golden/make_golden.py mid        # ~5 min, ~6 GB host RAM
+    python tests/golden/make_golden.py large3     # irregular, 4-word, 3-party; see LARGE3
 
 Every value written here comes from the CPU oracle (oracle/) run on a network
 drawn by paper_1801_05857_gb300.inputs; nothing comes from the CUDA path.
@@ -19,6 +20,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 # Mid network: inputs.WORKLOADS["mid"] (10 x 16 states, 2-word vectors, 4 two-party rules)
 MID = inputs.WORKLOADS["mid"]
+
+# Irregular memory-scaled-shape network: 16 processes x 16 local states (3 words, in 4-word
+# slots), 3 of 30 labels as 3-party rules (10 %), out-degree 1-2, local edges inside blocks
+# of 5 states and rule edges weighted 6:1 so that the rules fire: 1.08e8 states, 3.5 times
+# as many as the same network without its rule edges (the reachable set is no product of
+# the blocks).  ~12 GB of host RAM.
+LARGE3 = dict(seed=6, n_procs=16, n_states=16, deg_lo=1, deg_hi=2, n_labels=30, n_sync=3, parties=3,
+              cluster=5, sync_weight=6.0, name="large3_s6_n16")
 
 
 def write(name: str, gen: dict) -> None:
@@ -60,5 +69,7 @@ if __name__ == "__main__":
     which = sys.argv[1:] or ["mid"]
     if "mid" in which:
         write("mid_network.json", MID)
+    if "large3" in which:
+        write("large3_network.json", LARGE3)
     if "batch" in which:
         write_batch()
