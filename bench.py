@@ -48,16 +48,17 @@ def parse():
     ap.add_argument("--nodes", type=int, default=19, help="token-ring nodes for --experiment scaled")
     ap.add_argument("--family", default="ring", choices=["ring", "product"],
                     help="--experiment scaled: token ring (--nodes) or the memory-scaled product network")
-    ap.add_argument("--warp-cache", type=int, default=9,
-                    help="log2 entries of the per-warp cache of seen vectors (0 = off)")
+    ap.add_argument("--warp-cache", type=int, default=-1,
+                    help="log2 entries of the per-warp cache of seen vectors (0 = off, -1 = automatic)")
     ap.add_argument("--level-loop", default="host", choices=["host", "device"],
                     help="main line: levels driven by the host (profilable kernel by kernel) or by "
                          "the device (one CUDA graph); the other one is timed beside it")
-    ap.add_argument("--global-cache", type=int, default=0,
-                    help="log2 entries of the GPU-wide cache of seen vectors (0 = off)")
+    ap.add_argument("--global-cache", type=int, default=-1,
+                    help="log2 entries of the GPU-wide cache of seen vectors (0 = off, -1 = automatic)")
     ap.add_argument("--region-passes", type=int, default=0,
                     help="passes per level, each probing one region of the table (0 = auto: regions "
                          "of at most 64 GiB)")
+    ap.add_argument("--max-levels", type=int, default=0, help="--experiment search: stop after this many levels")
     ap.add_argument("--partition-min", type=int, default=0,
                     help="partition levels with at least this many states (0 = never)")
     ap.add_argument("--cpu-sample", type=int, default=3_000_000,
@@ -68,13 +69,16 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided deadlock-search part")
     ap.add_argument("--experiment", default="", choices=["", "table-sweep", "cuckoo-sweep", "bucket-sweep", "scaled", "scaling-table", "scorer", "batch",
-                             "guided", "cache-sweep"],
+                             "guided", "cache-sweep", "guided-compare", "search"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
                          "exploration for every (bucket, group) size; scaled: one large token ring; "
                          "scaling-table: ring and producer/consumer families by size (Table 1); "
                          "scorer: the tensor-core scoring kernel alone; batch: the 256-network batch "
                          "alone; guided: one guided search with a host round trip per iteration; "
                          "cache-sweep: --workload for per-warp and GPU-wide cache sizes; "
+                         "guided-compare: guided search with the scoring in its own kernel and fused "
+                         "into the expansion, 12-16 processes; search: one warm-up and one timed search of "
+                         "--workload (host level loop, at most --max-levels levels), for profiling; "
                          "one JSON line per point")
     args = ap.parse_args()
     wl = WORKLOAD_SETTINGS.get(args.workload, WORKLOAD_SETTINGS["mid"])
@@ -453,10 +457,10 @@ def guided_part(torch, gx, inputs, guide) -> dict:
     untrained = torch.empty(gx.MLP_PARAMS, dtype=torch.float32, device="cuda")
     gx.mlp_init(untrained, 99)
 
-    def guided(net, p):
+    def guided(net, p, fused=0):
         h = gx.load_network(net)
         gx.guided_set_weights(h, p)
-        o = gx.default_opts(table_bytes=2 << 30, hash_rounds=32)
+        o = gx.default_opts(table_bytes=2 << 30, hash_rounds=32, guided_fused=fused)
         ws = gx.guided_alloc_workspace(h, o)
         try:
             n, _ = gx.find_deadlocks(h, gx.GX_DL_GUIDED, o, ws)
@@ -497,7 +501,9 @@ def guided_part(torch, gx, inputs, guide) -> dict:
             # the guided search is not deterministic (concurrent pushes order the bins):
             # five runs per seed; the untrained guide and BFS once
             runs = [guided(net, params) for _ in range(5)]
-            per.append({"network": net.name, "guided_runs": runs, "untrained": guided(net, untrained),
+            fused_runs = [guided(net, params, fused=1) for _ in range(5)]
+            per.append({"network": net.name, "guided_runs": runs, "fused_runs": fused_runs,
+                        "untrained": guided(net, untrained),
                         "bfs": bfs(net, 24 if n <= 14 else 128)})
         rows.extend(per)
 
@@ -506,12 +512,16 @@ def guided_part(torch, gx, inputs, guide) -> dict:
             return v[len(v) // 2] if v else None
 
         g_runs = [x for r in per for x in r["guided_runs"] if x.get("found")]
+        f_runs = [x for r in per for x in r["fused_runs"] if x.get("found")]
         summary.append({"processes": n, "planted_deadlocks": k, "seeds": 5, "guided_runs_per_seed": 5,
                         "guided_found": len(g_runs),
                         "guided_median_explored": med([x["explored"] for x in g_runs]),
                         "guided_median_ms": med([x["ms"] for x in g_runs]),
                         "guided_ms_range": [min(x["ms"] for x in g_runs), max(x["ms"] for x in g_runs)]
                         if g_runs else None,
+                        "fused_found": len(f_runs),
+                        "fused_median_explored": med([x["explored"] for x in f_runs]),
+                        "fused_median_ms": med([x["ms"] for x in f_runs]),
                         **{f"{arm}_found": sum(1 for r in per if r[arm].get("found")) for arm in ("untrained", "bfs")},
                         **{f"{arm}_median_{key}": med([r[arm][key] for r in per if r[arm].get("found")])
                            for arm in ("untrained", "bfs") for key in ("explored", "ms")}})
@@ -622,8 +632,8 @@ def search_opts(gx, args, host_loop: bool, table_log2_words: int | None = None):
     return gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
                            table_bytes=4 << (table_log2_words or args.table_log2_words),
                            slice_log2=args.slice_log2, partition_min_states=args.partition_min,
-                           warp_cache_log2=args.warp_cache, region_passes=args.region_passes,
-                           global_cache_log2=args.global_cache, host_loop=int(host_loop))
+                           warp_cache_log2=args.warp_cache & 0xFFFFFFFF, region_passes=args.region_passes,
+                           global_cache_log2=args.global_cache & 0xFFFFFFFF, host_loop=int(host_loop))
 
 
 def time_searches(torch, gx, h, opts, ws, steps: int) -> dict:
@@ -909,8 +919,8 @@ def scaled_experiment(torch, gx, inputs, args):
     h = gx.load_network(net)
     o = gx.default_opts(bucket_words=args.bucket, group_lanes=args.group, hash_rounds=args.rounds,
                         table_bytes=4 << args.table_log2_words, slice_log2=args.slice_log2,
-                        partition_min_states=args.partition_min, warp_cache_log2=args.warp_cache,
-                        region_passes=args.region_passes, global_cache_log2=args.global_cache)
+                        partition_min_states=args.partition_min, warp_cache_log2=args.warp_cache & 0xFFFFFFFF,
+                        region_passes=args.region_passes, global_cache_log2=args.global_cache & 0xFFFFFFFF)
     ws = gx.alloc_workspace(h, o)
     gx.explore(h, o, ws)
     s = gx.stats(h)
@@ -1068,6 +1078,52 @@ def run_experiment(args):
         scaling_table(torch, gx, inputs, args)
     elif args.experiment == "scaled":
         scaled_experiment(torch, gx, inputs, args)
+    elif args.experiment == "guided-compare":
+        # the guided search's two kernel layouts on the bench's planted networks: median over
+        # 5 seeds x 5 runs of states explored and time to the first deadlock
+        from paper_1801_05857_gb300 import guide
+        train_nets = [inputs.planted_network(s, n, n_traps=1 + s % 4) for s in range(6) for n in (6, 7, 8)]
+        hist, label = guide.collect_examples(train_nets, 64)
+        params, _ = guide.train(hist, label, steps=4000, lr=1e-3)
+        for n, k in ((12, 2), (13, 2), (14, 2), (16, 3)):
+            res = {}
+            for fused in (0, 1):
+                ms, ex, it = [], [], []
+                for seed in range(5):
+                    net = inputs.planted_network(seed, n, n_traps=k)
+                    h = gx.load_network(net)
+                    gx.guided_set_weights(h, params)
+                    o = gx.default_opts(table_bytes=2 << 30, hash_rounds=32, guided_fused=fused)
+                    ws = gx.guided_alloc_workspace(h, o)
+                    for _ in range(5):
+                        nf, _ = gx.find_deadlocks(h, gx.GX_DL_GUIDED, o, ws)
+                        s2 = gx.stats(h)
+                        if nf:
+                            ms.append(s2["gpu_ms"])
+                            ex.append(s2["explored"])
+                            it.append(s2["expand_launches"])
+                    del ws
+                    torch.cuda.empty_cache()
+                ms.sort(), ex.sort(), it.sort()
+                res["fused" if fused else "split"] = {"found": len(ms), "median_ms": round(ms[len(ms) // 2], 3) if ms else None,
+                                                      "median_explored": ex[len(ex) // 2] if ex else None,
+                                                      "median_iterations": it[len(it) // 2] if it else None}
+            print(json.dumps({"experiment": "guided-compare", "processes": n, **res}), flush=True)
+    elif args.experiment == "search":
+        net = inputs.workload(args.workload)
+        h = gx.load_network(net)
+        o = search_opts(gx, args, host_loop=True)
+        o.max_levels = args.max_levels
+        ws = gx.alloc_workspace(h, o)
+        for _ in range(2):
+            gx.explore(h, o, ws)
+        s = gx.stats(h)
+        bytes_alg = algorithmic_bytes(s)
+        print(json.dumps({"experiment": "search", "workload": args.workload, "table_gib": round(4 * (1 << args.table_log2_words) / 2 ** 30, 2),
+                          "levels": s["n_levels"], "expand_launches": s["expand_launches"], "states": s["states"],
+                          "explored": s["explored"], "transitions": s["transitions"], "probes": s["probes"],
+                          "region_passes": s["region_passes"], "fill": round(s["fill"], 4),
+                          "algorithmic_bytes": bytes_alg, "gpu_ms": round(s["gpu_ms"], 3)}), flush=True)
     elif args.experiment == "cache-sweep":
         # per-warp cache x GPU-wide cache sizes on --workload (device level loop), median of
         # --steps searches after --warmup
@@ -1102,7 +1158,7 @@ def run_experiment(args):
             while bucket >= W and group <= bucket // W:
                 o = gx.default_opts(bucket_words=bucket, group_lanes=group, hash_rounds=args.rounds,
                                     table_bytes=4 << args.table_log2_words,
-                                    warp_cache_log2=args.warp_cache)
+                                    warp_cache_log2=args.warp_cache & 0xFFFFFFFF)
                 ws = gx.alloc_workspace(h, o)
                 ts = []
                 for _ in range(args.warmup + args.steps):

@@ -171,9 +171,9 @@ typedef struct gx_explore_opts {
   uint32_t warp_cache_log2;      /* per-warp cache of recently seen vectors (the block-local
                                     state cache of Fig. 2): 2^n entries per warp in shared
                                     memory (2^(n-1) for 4-word vectors, the same bytes), a hit
-                                    skips find-or-put.  0 = off, 0xFFFFFFFF = 2^9;
-                                    gx_default_opts sets 9 (mid network: 21 % fewer bucket
-                                    reads, 8 % faster) */
+                                    skips find-or-put.  0 = off, 1..12 = 2^n, 0xFFFFFFFF =
+                                    automatic (gx_default_opts): 2^9 unless the GPU-wide
+                                    cache below is in use (together they measured slower) */
   float guided_scale;            /* GX_DL_GUIDED: score at which a state falls in the last
                                     bin (scores are predicted distances / max_dist); 0 = 1.0 */
   uint32_t watch;                /* 1 = safety check (Sec. 3: the negation of a safety property
@@ -210,11 +210,18 @@ typedef struct gx_explore_opts {
                                     goes in after its find-or-put found or inserted it, so a
                                     hit is a known state and skips the table probe; most
                                     successors of a level lead into the levels just before
-                                    and after it.  0 = off (gx_default_opts), 0xFFFFFFFF =
-                                    2^20, at most 2^26.  Off by default: on the mid network
-                                    2^23 entries cut bucket reads per successor from 0.82 to
-                                    0.30, but the search is bound by successor generation
-                                    there and takes as long (22.4 against 21.5 ms) */
+                                    and after it.  0 = off, 1..26 = 2^n, 0xFFFFFFFF =
+                                    automatic (gx_default_opts): 2^23 entries (64 MiB) for
+                                    1- and 2-word vectors in tables of at least 2^26 slots
+                                    with one lane per bucket (group_lanes 1), else off.  Mid network: 0.36 bucket reads per successor
+                                    and 18.9 ms, against 0.82 and 20.4 ms with the per-warp
+                                    cache; small sizes (2^14-2^18) are far slower, many warps
+                                    writing the same few lines */
+  uint32_t guided_fused;         /* GX_DL_GUIDED: 1 = score the states an iteration inserts
+                                    inside its expansion kernel (each CTA keeps them in shared
+                                    memory and scores 128 at a time on the tensor cores), 0 =
+                                    a separate scoring kernel over a pending buffer.  The
+                                    search is the same either way */
 } gx_explore_opts;
 
 /* Fill *opts with the defaults described above. */

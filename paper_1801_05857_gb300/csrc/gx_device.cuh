@@ -50,7 +50,10 @@ __device__ __forceinline__ uint64_t vec_hash(const uint32_t (&v)[W]) {
   } else if constexpr (W == 2) {
     x = (uint64_t)v[0] | ((uint64_t)v[1] << 32);
   } else {
-    x = mix64((uint64_t)v[0] | ((uint64_t)v[1] << 32)) ^ ((uint64_t)v[2] | ((uint64_t)v[3] << 32));
+    // the upper half multiplied by an odd constant (a bijection), added to the lower
+    // half, then one finaliser: one mix64 per vector instead of two
+    x = ((uint64_t)v[0] | ((uint64_t)v[1] << 32)) +
+        ((uint64_t)v[2] | ((uint64_t)v[3] << 32)) * 0xD6E8FEB86659FD93ull;
   }
   return mix64(x);
 }
@@ -158,16 +161,16 @@ struct Group {
 // is increased by the number of buckets read (once per bucket, not per lane).
 // With PRE, `pre` already holds this lane's part of the first bucket (read by
 // the caller, and counted there), so round 0 starts without a load.
+// find_or_put_hashed takes h = vec_hash(v) from the caller.
 template <int W, int B, int G, bool PRE>
-__device__ __forceinline__ int find_or_put_from(uint32_t* __restrict__ table, int log2nb, int rounds,
-                                                const uint64_t* __restrict__ muls,
-                                                const uint32_t (&v)[W], const Group<G>& g,
-                                                uint32_t& probes, const uint32_t (&pre)[(B / W / G) * W]) {
+__device__ __forceinline__ int find_or_put_hashed(uint32_t* __restrict__ table, int log2nb, int rounds,
+                                                  const uint64_t* __restrict__ muls,
+                                                  const uint32_t (&v)[W], const uint64_t h, const Group<G>& g,
+                                                  uint32_t& probes, const uint32_t (&pre)[(B / W / G) * W]) {
   constexpr int S = B / W;
   static_assert(S >= 1 && S % G == 0, "group size must divide the slots per bucket");
   constexpr int SPL = S / G;
   constexpr int LW = SPL * W;
-  const uint64_t h = vec_hash<W>(v);
   for (int k = 0; k < rounds; ++k) {
     const uint64_t b = bucket_of(h, muls[k], log2nb);
     uint32_t* lane_slots = table + b * (uint64_t)B + (uint64_t)g.glane * LW;
@@ -218,6 +221,14 @@ __device__ __forceinline__ int find_or_put_from(uint32_t* __restrict__ table, in
     }
   }
   return FOP_FULL;
+}
+
+template <int W, int B, int G, bool PRE>
+__device__ __forceinline__ int find_or_put_from(uint32_t* __restrict__ table, int log2nb, int rounds,
+                                                const uint64_t* __restrict__ muls,
+                                                const uint32_t (&v)[W], const Group<G>& g,
+                                                uint32_t& probes, const uint32_t (&pre)[(B / W / G) * W]) {
+  return find_or_put_hashed<W, B, G, PRE>(table, log2nb, rounds, muls, v, vec_hash<W>(v), g, probes, pre);
 }
 
 template <int W, int B, int G>

@@ -201,6 +201,7 @@ constexpr int kPartCtas = 1024;  // CTAs of the partitioned count/scatter passes
 // 32-byte reads run at the full rate over any 64 GiB of a table and 4x slower
 // over 128 GiB (the GPU's address-translation reach).
 constexpr uint64_t kAutoRegionBytes = 64ull << 30;
+constexpr uint32_t kAutoCache = 0xFFFFFFFFu;  // warp_cache_log2 / global_cache_log2: automatic
 
 // Arguments of pass q of `passes` region passes over a table of 2^log2nb buckets.
 inline ExpandArgs region_pass(const ExpandArgs& a, uint32_t passes, uint32_t q) {
@@ -225,6 +226,7 @@ struct Plan {
   uint64_t part_min = 0;   // smallest level that may use the partitioned path
   uint32_t regions = 1;    // passes per level of the direct path (region passes)
   uint64_t gcache = 0;     // entries of the GPU-wide cache of seen vectors (0 = off)
+  uint32_t warp_log2 = 0;  // per-warp cache of seen vectors: 2^warp_log2 entries (0 = off)
   uint64_t off_ctl = 0, off_blob = 0, off_dl = 0, off_viol = 0, off_loop = 0, off_front = 0, off_table = 0;
   uint64_t off_hist = 0, off_off = 0, off_ptot = 0, off_tot = 0, off_succ = 0, off_gcache = 0;
   uint64_t total = 0;
@@ -287,11 +289,16 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
     while (P.regions < 16 && tbytes / P.regions > kAutoRegionBytes) P.regions *= 2;
   }
   if (P.regions > P.nb) P.regions = (uint32_t)P.nb;
-  if (o->global_cache_log2) {
-    const uint32_t k = o->global_cache_log2 == 0xFFFFFFFFu ? 20 : o->global_cache_log2;
-    if (k > 26) return fail(GX_ERR_INVALID, "global_cache_log2 must be at most 26");
-    if (P.W <= 2) P.gcache = 1ull << k;  // 4-word vectors: not used
+  // the caches of seen vectors: auto = the GPU-wide one (2^23 entries) for 1- and
+  // 2-word vectors in tables of at least 2^26 slots with one lane per bucket (where it
+  // was measured), else the per-warp one (2^9)
+  if (o->global_cache_log2 == kAutoCache) {
+    if (P.W <= 2 && P.G == 1 && slots >= (1ull << 26)) P.gcache = 1ull << 23;
+  } else if (o->global_cache_log2) {
+    if (o->global_cache_log2 > 26) return fail(GX_ERR_INVALID, "global_cache_log2 must be at most 26");
+    if (P.W <= 2) P.gcache = 1ull << o->global_cache_log2;  // 4-word vectors: not used
   }
+  P.warp_log2 = o->warp_cache_log2 == kAutoCache ? (P.gcache ? 0u : 9u) : o->warp_cache_log2;
   P.cs = o->successor_buffer ? o->successor_buffer : std::min<uint64_t>(slots / 2, (1ull << 32) - 1);
   if (P.logp == 0) P.cs = 0;  // partitioned path off: no buffer
   if (P.cs >= (1ull << 32)) return fail(GX_ERR_INVALID, "successor_buffer must be below 2^32 vectors");
@@ -561,8 +568,8 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   ea.stage = (smem + blob_bytes <= std::min<size_t>(dev.smem_optin, 96 * 1024)) ? 1 : 0;
   if (ea.stage) smem += blob_bytes;
   ea.cache_log2 = 0;
-  if (o->warp_cache_log2) {
-    ea.cache_log2 = o->warp_cache_log2 == 0xFFFFFFFFu ? 9 : (int)o->warp_cache_log2;
+  if (P.warp_log2) {
+    ea.cache_log2 = (int)P.warp_log2;
     if (ea.cache_log2 > 12) return fail(GX_ERR_INVALID, "warp_cache_log2 must be at most 12");
     if (P.W == 4) ea.cache_log2 -= 1;  // 16-byte entries: the same bytes as 2^n 2-word ones
     smem += 4ull * P.W * (kBlock / 32) * (1ull << ea.cache_log2);

@@ -551,6 +551,198 @@ __global__ void __launch_bounds__(gxt::kRows) guided_score_kernel(const GuidedAr
   if (err) atomicOr(&a.ctl->error, err);
 }
 
+// Expansion and scoring in one kernel (gx_explore_opts.guided_fused): the
+// same one-warp-per-state expansion as guided_expand_kernel, but a CTA keeps
+// the states its warps insert, with their histograms, in shared memory, and
+// its warps 0-3 score them 128 at a time on the tensor cores (gx_tc.cuh,
+// synchronising among themselves on a named barrier) and push them to their
+// bins -- no pending buffer and no scoring kernel.  The warps of a CTA walk
+// their states' successors in lock-step chunks of 32 (a CTA barrier after each
+// chunk), so at most 127 + 16 x 32 states wait for a tile.
+constexpr int kFusedWarps = 16;
+constexpr int kFusedThreads = kFusedWarps * 32;
+constexpr int kFusedRows = gxt::kRows - 1 + kFusedThreads;
+
+template <int W>
+__host__ __device__ constexpr size_t fused_smem_bytes(size_t blob_bytes) {
+  return gxt::kTcSmemBytes + 16ull * kFusedRows + 4ull * (W + 1) * kFusedRows + blob_bytes;
+}
+
+template <int W, int B>
+__global__ void __launch_bounds__(kFusedThreads, 2) guided_fused_kernel(const GuidedArgs a) {
+  constexpr int E = W + 1;
+  const unsigned long long n = a.ctl->batch_n;
+  const unsigned long long nwarps = (unsigned long long)gridDim.x * kFusedWarps;
+  if ((unsigned long long)blockIdx.x * kFusedWarps >= n) return;  // no state for this CTA
+  extern __shared__ __align__(16) uint8_t fsm[];
+  uint8_t* tc_area = fsm;  // the scorer's 1024-aligned part lies within its first kTcSmemBytes
+  uint4* rows_h = reinterpret_cast<uint4*>(fsm + gxt::kTcSmemBytes);
+  uint32_t* rows_e = reinterpret_cast<uint32_t*>(rows_h + kFusedRows);
+  uint32_t* s_tab = rows_e + E * kFusedRows;
+  __shared__ uint64_t muls[kMaxRounds];
+  __shared__ unsigned int s_rows, s_steps, s_ok;
+  __shared__ unsigned long long s_sum[3][kFusedWarps];
+  __shared__ uint32_t s_err[kFusedWarps];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int i = tid; i < a.rounds; i += blockDim.x) muls[i] = a.muls.m[i];
+  const uint32_t* t = a.blob;
+  if (a.stage) {
+    for (uint32_t i = tid; i < a.blob_words; i += blockDim.x) s_tab[i] = a.blob[i];
+    t = s_tab;
+  }
+  uint32_t err = 0;
+  gxt::TcScorer sc{};
+  if (tid < gxt::kRows) {
+    sc = gxt::tc_setup(tc_area, a.tcw);
+    if (tid == 0) s_ok = sc.ok ? 1u : 0u;
+  }
+  if (tid == 0) s_rows = 0;
+  __syncthreads();
+  if (!s_ok) err |= gx::ERR_SPIN;
+  const NetBlobLayout& L = a.lay;
+  const Group<1> g;
+  const unsigned long long log_base = a.ctl->log_base;
+  unsigned long long trans = 0, ins = 0;
+  uint32_t probes = 0;
+
+  // Score rows [0, m) (m <= 128) with the scoring threads and push them to their bins.
+  auto score_rows = [&](unsigned int m) {
+    if (tid < gxt::kRows && s_ok) {
+      uint32_t hw[4] = {0, 0, 0, 0};
+      const bool valid = (unsigned int)tid < m;
+      if (valid) {
+        const uint4 q = rows_h[tid];
+        hw[0] = q.x;
+        hw[1] = q.y;
+        hw[2] = q.z;
+        hw[3] = q.w;
+      }
+      float y = 0.f;
+      if (!gxt::tc_score_tile(sc, hw, y)) {
+        err |= gx::ERR_SPIN;
+        if (tid == 0) s_ok = 0;
+      } else if (valid) {
+        uint32_t v[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) v[w] = rows_e[tid * E + w];
+        push_bin<W>(a, y, v, rows_e[tid * E + W], err);
+      }
+    }
+  };
+
+  const unsigned long long first = (unsigned long long)blockIdx.x * kFusedWarps;
+  const unsigned long long rounds = (n - first + nwarps - 1) / nwarps;  // the same for the whole CTA
+  for (unsigned long long r = 0; r < rounds; ++r) {
+    const unsigned long long idx = first + wid + r * nwarps;
+    const bool has = idx < n;
+    uint32_t v[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) v[w] = has ? a.batch[idx * E + w] : 0u;
+    const unsigned long long li = log_base + idx;
+    uint32_t total = 0;
+    if (has) {
+      if (lane == 0) {
+        uint32_t* le = a.log + li * E;
+#pragma unroll
+        for (int w = 0; w < W; ++w) le[w] = v[w];
+        le[W] = a.batch[idx * E + W];
+      }
+      total = count_succ<W>(t, L, v);
+      if (lane == 0) {
+        trans += total;
+        if (total == 0) {
+          atomicMin(&a.ctl->found, li);
+          atomicAdd(&a.ctl->dl_count, 1ull);
+        }
+      }
+    }
+    if (tid == 0) s_steps = 0;
+    __syncthreads();
+    if (lane == 0 && total) atomicMax(&s_steps, (total + 31u) / 32u);
+    __syncthreads();
+    const uint32_t steps = s_steps;
+    for (uint32_t c = 0; c < steps; ++c) {
+      const uint32_t k = c * 32 + lane;
+      uint32_t s[W];
+      bool inserted = false;
+      if (k < total) {
+        seek_succ<W>(t, L, v, k, s);
+        const int res = find_or_put<W, B, 1>(a.table, a.log2nb, a.rounds, muls, s, g, probes);
+        if (res == FOP_FULL) err |= gx::ERR_TABLE_FULL;
+        inserted = res == FOP_INSERTED;
+      }
+      uint32_t hw[4] = {0, 0, 0, 0}, bad = 0;
+      if (inserted) local_hist<W>(t, L, s, hw, bad);
+      if (bad) err |= gx::ERR_WIDE;
+      const uint32_t im = __ballot_sync(FULLMASK, inserted);
+      ins += inserted ? 1u : 0u;
+      if (im) {  // rows for the warp's new states, one shared-memory atomic per warp
+        unsigned int base = 0;
+        if (lane == 0) base = atomicAdd(&s_rows, (unsigned int)__popc(im));
+        base = __shfl_sync(FULLMASK, base, 0);
+        if (inserted) {
+          const unsigned int row = base + __popc(im & ((1u << lane) - 1u));
+          rows_h[row] = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+#pragma unroll
+          for (int w = 0; w < W; ++w) rows_e[row * E + w] = s[w];
+          rows_e[row * E + W] = (uint32_t)li;
+        }
+      }
+      __syncthreads();
+      // full tiles: score rows [0, 128), move the rest to the front
+      while (s_rows >= (unsigned int)gxt::kRows) {
+        const unsigned int m = s_rows;
+        score_rows(gxt::kRows);
+        __syncthreads();
+        const unsigned int left = m - gxt::kRows;  // < 16 x 32
+        uint4 hq = make_uint4(0, 0, 0, 0);
+        uint32_t eq[E];
+        if ((unsigned int)tid < left) {
+          hq = rows_h[gxt::kRows + tid];
+#pragma unroll
+          for (int w = 0; w < E; ++w) eq[w] = rows_e[(gxt::kRows + tid) * E + w];
+        }
+        __syncthreads();
+        if ((unsigned int)tid < left) {
+          rows_h[tid] = hq;
+#pragma unroll
+          for (int w = 0; w < E; ++w) rows_e[tid * E + w] = eq[w];
+        }
+        if (tid == 0) s_rows = left;
+        __syncthreads();
+      }
+    }
+  }
+  if (s_rows > 0) score_rows(s_rows);  // the last, partial tile
+  if (tid < gxt::kRows) gxt::tc_teardown(sc);
+  // the CTA's totals, one atomic per counter
+  trans = warp_sum(trans);
+  ins = warp_sum(ins);
+  const unsigned long long pr = warp_sum((unsigned long long)probes);
+  err = __reduce_or_sync(FULLMASK, err);
+  if (lane == 0) {
+    s_sum[0][wid] = trans;
+    s_sum[1][wid] = ins;
+    s_sum[2][wid] = pr;
+    s_err[wid] = err;
+  }
+  __syncthreads();
+  if (tid < 4) {
+    unsigned long long x = 0;
+    for (int w = 0; w < kFusedWarps; ++w) x += tid < 3 ? s_sum[tid][w] : (unsigned long long)s_err[w];
+    if (x) {
+      if (tid == 0) atomicAdd(&a.ctl->transitions, x);
+      else if (tid == 1) atomicAdd(&a.ctl->inserted, x);
+      else if (tid == 2) atomicAdd(&a.ctl->probes, x);
+      else {
+        uint32_t e = 0;
+        for (int w = 0; w < kFusedWarps; ++w) e |= s_err[w];
+        atomicOr(&a.ctl->error, e);
+      }
+    }
+  }
+}
+
 // ---- the device-driven iteration loop and the deadlock's path
 
 // Control block at the start of a search (the rest was cleared).
@@ -629,6 +821,7 @@ struct GKernels {
   const void* path;
   const void* start;    // pop the first batch and start the device loop
   const void* advance;  // end an iteration and pop the next batch
+  const void* fused;    // expansion with the scoring in the same kernel
 };
 
 template <int W, int B>
@@ -639,7 +832,8 @@ GKernels gk() {
                   reinterpret_cast<const void*>(&gxd::guided_score_kernel<W>),
                   reinterpret_cast<const void*>(&gxd::guided_path_kernel<W>),
                   reinterpret_cast<const void*>(&gxd::guided_loop_start_kernel<W>),
-                  reinterpret_cast<const void*>(&gxd::guided_advance_kernel<W>)};
+                  reinterpret_cast<const void*>(&gxd::guided_advance_kernel<W>),
+                  reinterpret_cast<const void*>(&gxd::guided_fused_kernel<W, B>)};
 }
 
 bool gk_lookup(int W, int B, GKernels& k) {
@@ -733,7 +927,8 @@ namespace {
 // One guided search as a graph: clear the control block, bins and table,
 // insert the initial state, pop the first batch, then WHILE(cond) {expand,
 // score, advance (which pops the next batch)}.
-gx_status build_guided_graph(gx_net* h, const GPlan& P, GuidedArgs a, int grid, size_t smem, int score_grid) {
+gx_status build_guided_graph(gx_net* h, const GPlan& P, GuidedArgs a, int grid, size_t smem, int score_grid,
+                             bool fused, int fused_grid, size_t fused_smem) {
   release_guided(h);
   h->release_guided = &release_guided;
   cudaGraph_t g;
@@ -796,9 +991,14 @@ gx_status build_guided_graph(gx_net* h, const GPlan& P, GuidedArgs a, int grid, 
   cp.conditional.size = 1;
   GG_CUDA(cudaGraphAddNode(&cnode, g, &start, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  GG_CUDA(add_kernel(body, nullptr, 0, P.k.expand, dim3(grid), dim3(kBlock), smem, &ex));
-  GG_CUDA(add_kernel(body, &ex, 1, P.k.score, dim3(score_grid), dim3(gxt::kRows), gxt::kTcSmemBytes, &sc));
-  GG_CUDA(add_kernel(body, &sc, 1, P.k.advance, dim3(1), dim3(1024), 0, &adv));
+  if (fused) {
+    GG_CUDA(add_kernel(body, nullptr, 0, P.k.fused, dim3(fused_grid), dim3(gxd::kFusedThreads), fused_smem, &ex));
+    GG_CUDA(add_kernel(body, &ex, 1, P.k.advance, dim3(1), dim3(1024), 0, &adv));
+  } else {
+    GG_CUDA(add_kernel(body, nullptr, 0, P.k.expand, dim3(grid), dim3(kBlock), smem, &ex));
+    GG_CUDA(add_kernel(body, &ex, 1, P.k.score, dim3(score_grid), dim3(gxt::kRows), gxt::kTcSmemBytes, &sc));
+    GG_CUDA(add_kernel(body, &sc, 1, P.k.advance, dim3(1), dim3(1024), 0, &adv));
+  }
   cudaGraphExec_t exec;
   GG_CUDA(cudaGraphInstantiate(&exec, g, 0));
   h->guided_exec = exec;
@@ -859,6 +1059,22 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
   GG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.k.expand, kBlock, smem));
   const int grid = sms * std::max(per_sm, 1);
   const int score_grid = sms * gxt::tc_ctas_per_sm(dev);
+  // the fused kernel: its shared memory holds the scorer, the staged rows and the blob
+  const bool fused = opts && opts->guided_fused;
+  auto fused_bytes = [&](size_t b) {
+    return P.W == 1 ? gxd::fused_smem_bytes<1>(b) : P.W == 2 ? gxd::fused_smem_bytes<2>(b) : gxd::fused_smem_bytes<4>(b);
+  };
+  size_t fused_smem = 0;
+  int fused_grid = 0;
+  if (fused) {
+    a.stage = fused_bytes(blob_bytes) <= (size_t)optin ? 1 : 0;  // else the tables are read from global memory
+    fused_smem = fused_bytes(a.stage ? blob_bytes : 0);
+    GG_CUDA(cudaFuncSetAttribute(P.k.fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fused_smem));
+    int fp = 0;
+    GG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fp, P.k.fused, gxd::kFusedThreads, fused_smem));
+    fp = std::min(std::max(fp, 1), 4);  // TMEM: 128 columns per CTA, 512 per SM
+    fused_grid = sms * fp;
+  }
 
   cudaEvent_t e0, e1;
   GG_CUDA(cudaEventCreate(&e0));
@@ -877,7 +1093,7 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
     if (opts) std::memcpy(key.data(), opts, sizeof(gx_explore_opts));
     std::memcpy(key.data() + sizeof(gx_explore_opts), extra, sizeof(extra));
     if (!h->guided_exec || h->guided_key != key) {
-      s = build_guided_graph(h, P, a, grid, smem, score_grid);
+      s = build_guided_graph(h, P, a, grid, smem, score_grid, fused, fused_grid, fused_smem);
       if (s != GX_OK) return s;
       h->guided_key = key;
     }
@@ -894,8 +1110,12 @@ gx_status run_guided(gx_net* h, const gx_explore_opts* opts, void* ws, uint64_t 
     GG_CUDA(cudaLaunchKernel(P.k.init, dim3(1), dim3(32), args, 0, st));
     while (true) {
       GG_CUDA(cudaLaunchKernel(P.k.select, dim3(1), dim3(1024), args, 0, st));
-      GG_CUDA(cudaLaunchKernel(P.k.expand, dim3(grid), dim3(kBlock), args, smem, st));
-      GG_CUDA(cudaLaunchKernel(P.k.score, dim3(score_grid), dim3(gxt::kRows), args, gxt::kTcSmemBytes, st));
+      if (fused) {
+        GG_CUDA(cudaLaunchKernel(P.k.fused, dim3(fused_grid), dim3(gxd::kFusedThreads), args, fused_smem, st));
+      } else {
+        GG_CUDA(cudaLaunchKernel(P.k.expand, dim3(grid), dim3(kBlock), args, smem, st));
+        GG_CUDA(cudaLaunchKernel(P.k.score, dim3(score_grid), dim3(gxt::kRows), args, gxt::kTcSmemBytes, st));
+      }
       GG_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(hc), cudaMemcpyDeviceToHost, st));
       GG_CUDA(cudaStreamSynchronize(st));
       ++iters;

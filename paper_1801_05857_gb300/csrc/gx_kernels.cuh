@@ -443,11 +443,21 @@ __device__ __forceinline__ void insert_lanes(const T& a, const uint64_t* muls,
         // region passes: a vector whose first bucket lies outside this pass's region is
         // left to the pass of that region (tested before the cache, which may only hold
         // vectors that went to find-or-put)
-        if ((b & a.region_mask()) != a.region_bits()) hv[j] = false;
-        // a vector this warp has already sent to find-or-put needs no second lookup
-        else if (cache.base && cache.template seen<W>(hh, x[j])) hv[j] = false;
-        // nor does one that any warp found or inserted moments ago
-        else if (W <= 2 && a.gcache() && gcache_hit<W>(a.gcache(), a.gcache_mask(), hh, x[j])) hv[j] = false;
+        if ((b & a.region_mask()) != a.region_bits()) {
+          hv[j] = false;
+        } else if (cache.base || (W <= 2 && a.gcache())) {
+          // A vector this warp has already sent to find-or-put needs no second lookup,
+          // nor does one that any warp found or inserted moments ago.  One lane of the
+          // group reads (and writes) the caches and the group takes its answer: other
+          // warps write the GPU-wide cache at any moment, and lanes of a group are not
+          // guaranteed to read it in one instruction, so their own reads could disagree
+          // and split the group before find-or-put's group-wide votes.
+          int known = 0;
+          if (g.glane == 0)
+            known = (cache.base && cache.template seen<W>(hh, x[j])) ||
+                    (W <= 2 && a.gcache() && gcache_hit<W>(a.gcache(), a.gcache_mask(), hh, x[j]));
+          if (g.template bcast<int>(known, g.base)) hv[j] = false;
+        }
         if (hv[j]) {
           load_words<LW>(a.table() + b * (uint64_t)B + (uint64_t)g.glane * LW, pre[j]);
           probes += g.glane == 0;
@@ -469,6 +479,44 @@ __device__ __forceinline__ void insert_lanes(const T& a, const uint64_t* muls,
 #pragma unroll
   for (int k = 0; k < K; ++k) st.push<W>(a, inserted[k], s[k], err);
 }
+
+// One lane per bucket (G = 1): find-or-put of the vector x of every lane with
+// has set (the filters of insert_lanes already passed), its new vectors staged
+// for the next level.  All 32 lanes call it together.
+template <int W, int B, class T>
+__device__ __forceinline__ void resolve_lanes(const T& a, const uint64_t* muls, bool has, const uint32_t (&x)[W],
+                                              const uint64_t hh, uint32_t& probes, uint32_t& err, WarpStage& st) {
+  constexpr int LW = (B / W) * W;
+  const Group<1> g;
+  bool inserted = false;
+  uint32_t pre[LW];
+  if (has) {
+    const uint64_t b = bucket_of(hh, muls[0], a.log2nb());
+    load_words<LW>(a.table() + b * (uint64_t)B, pre);
+    ++probes;
+    const int r = find_or_put_hashed<W, B, 1, true>(a.table(), a.log2nb(), a.rounds(), muls, x, hh, g, probes, pre);
+    if (r == FOP_FULL) err |= gx::ERR_TABLE_FULL;
+    else if (W <= 2 && a.gcache()) gcache_put<W>(a.gcache(), a.gcache_mask(), hh, x);
+    inserted = r == FOP_INSERTED;
+  }
+  st.push<W>(a, inserted, x, err);
+}
+
+// Per-warp queue of successors waiting for their find-or-put (G = 1).  The lanes
+// of a warp expand different states, whose successor counts differ: one
+// successor per lane and round leaves the lanes of the states with fewer
+// successors idle in the rounds that follow.  So each round only generates one
+// successor per lane and queues the ones the filters keep (region, per-warp
+// cache, GPU-wide cache); whenever 32 are queued, every lane resolves one, so
+// the bucket reads and compare-and-swaps run with all 32 lanes busy.
+constexpr int kQueue = 64;  // at most 31 left + 32 new
+
+template <int W>
+struct WarpQueue {
+  uint32_t* buf;             // kQueue * W words of this warp
+  unsigned long long* hash;  // kQueue hashes (vec_hash) of the queued vectors
+  int n;                     // queued vectors (uniform in the warp)
+};
 
 // Resident CTAs per SM the level kernel is compiled for (register budget).
 // A lane holds min(G, 4) first buckets in flight of B / G words each; up to
@@ -512,6 +560,9 @@ __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expa
   uint32_t probes = 0, err = 0;
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
+  __shared__ uint32_t queue_mem[G == 1 ? gx::kBlock / 32 : 1][G == 1 ? kQueue * W : 1];
+  __shared__ unsigned long long queue_hash[G == 1 ? gx::kBlock / 32 : 1][G == 1 ? kQueue : 1];
+  WarpQueue<W> wq{queue_mem[G == 1 ? threadIdx.x >> 5 : 0], queue_hash[G == 1 ? threadIdx.x >> 5 : 0], 0};
   const ParamTarget tg{a, s_range};
   WarpCache cache{nullptr, 0};
   if (a.cache_log2 > 0) {
@@ -549,23 +600,73 @@ __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expa
     if (a.watch && acct) check_watch<W>(a, t, L, v);
     SuccIter it;
     it.init();
-    constexpr int K = PerLane<G>::K;
-    while (__any_sync(FULLMASK, remaining != 0)) {
-      uint32_t s[K][W];
-      bool has[K];
-#pragma unroll
-      for (int k = 0; k < K; ++k) {
-        has[k] = remaining != 0;
-        if (has[k]) {
-          next_succ<W>(it, t, L, v, s[k]);
+    if constexpr (G == 1) {
+      while (__any_sync(FULLMASK, remaining != 0)) {
+        uint32_t x[W];
+        uint64_t hh = 0;
+        bool keep = remaining != 0;
+        if (keep) {
+          next_succ<W>(it, t, L, v, x);
           --remaining;
-        } else {
+          hh = vec_hash<W>(x);
+          const uint64_t b = bucket_of(hh, muls[0], a.log2nb);
+          // the filters of insert_lanes: region, per-warp cache, GPU-wide cache
+          if ((b & a.region_mask) != a.region_bits) keep = false;
+          else if (cache.base && cache.template seen<W>(hh, x)) keep = false;
+          else if (W <= 2 && a.gcache && gcache_hit<W>(a.gcache, a.gcache_mask, hh, x)) keep = false;
+        }
+        const uint32_t km = __ballot_sync(FULLMASK, keep);
+        if (keep) {
+          const int at = wq.n + __popc(km & ((1u << lane) - 1u));
 #pragma unroll
-          for (int w = 0; w < W; ++w) s[k][w] = 0;
+          for (int w = 0; w < W; ++w) wq.buf[at * W + w] = x[w];
+          wq.hash[at] = hh;
+        }
+        wq.n += __popc(km);
+        if (wq.n >= 32) {
+          __syncwarp();
+          uint32_t y[W];
+#pragma unroll
+          for (int w = 0; w < W; ++w) y[w] = wq.buf[lane * W + w];
+          resolve_lanes<W, B>(tg, muls, true, y, wq.hash[lane], probes, err, st);
+          __syncwarp();
+          if (lane < wq.n - 32) {
+#pragma unroll
+            for (int w = 0; w < W; ++w) wq.buf[lane * W + w] = wq.buf[(32 + lane) * W + w];
+            wq.hash[lane] = wq.hash[32 + lane];
+          }
+          wq.n -= 32;
+          __syncwarp();
         }
       }
-      insert_lanes<W, B, G, K>(tg, muls, g, has, s, probes, err, st, cache);
+    } else {
+      constexpr int K = PerLane<G>::K;
+      while (__any_sync(FULLMASK, remaining != 0)) {
+        uint32_t s[K][W];
+        bool has[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          has[k] = remaining != 0;
+          if (has[k]) {
+            next_succ<W>(it, t, L, v, s[k]);
+            --remaining;
+          } else {
+#pragma unroll
+            for (int w = 0; w < W; ++w) s[k][w] = 0;
+          }
+        }
+        insert_lanes<W, B, G, K>(tg, muls, g, has, s, probes, err, st, cache);
+      }
     }
+  }
+  if constexpr (G == 1) {  // what is left in the queue
+    __syncwarp();
+    const bool has = lane < wq.n;
+    uint32_t y[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) y[w] = has ? wq.buf[lane * W + w] : 0u;
+    resolve_lanes<W, B>(tg, muls, has, y, has ? wq.hash[lane] : 0ull, probes, err, st);
+    wq.n = 0;
   }
   st.flush<W>(tg, err);
   // the CTA's totals, one atomic per counter: at the end of a level every warp

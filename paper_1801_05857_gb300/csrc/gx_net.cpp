@@ -254,7 +254,8 @@ gx_status gx_default_opts(gx_explore_opts* o) {
   o->bucket_words = 8;
   o->hash_rounds = 8;
   o->deadlock_cap = 1024;
-  o->warp_cache_log2 = 9;
+  o->warp_cache_log2 = 0xFFFFFFFFu;    // automatic: see gx_explore_opts
+  o->global_cache_log2 = 0xFFFFFFFFu;
   return GX_OK;
 }
 

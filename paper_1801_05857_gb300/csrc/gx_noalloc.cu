@@ -105,12 +105,15 @@ gx_status gx_explore_noalloc(const gx_net* h, const gx_explore_opts* opts, void*
   const uint64_t fwant = o->frontier_states ? o->frontier_states : std::max<uint64_t>(4096, slots / 4);
   uint64_t fcap = 1;
   while (fcap < fwant) fcap *= 2;
-  uint64_t gentries = 0;  // GPU-wide cache of seen vectors (gx_explore_opts.global_cache_log2)
-  if (o->global_cache_log2) {
-    const uint32_t k = o->global_cache_log2 == 0xFFFFFFFFu ? 20 : o->global_cache_log2;
-    if (k > 26) return gx::fail(GX_ERR_INVALID, "global_cache_log2 must be at most 26");
-    if (W <= 2) gentries = 1ull << k;
+  // caches of seen vectors, as gx_explore chooses them (gx_explore_opts)
+  uint64_t gentries = 0;
+  if (o->global_cache_log2 == 0xFFFFFFFFu) {
+    if (W <= 2 && G == 1 && (table_bytes / (4ull * W)) >= (1ull << 26)) gentries = 1ull << 23;
+  } else if (o->global_cache_log2) {
+    if (o->global_cache_log2 > 26) return gx::fail(GX_ERR_INVALID, "global_cache_log2 must be at most 26");
+    if (W <= 2) gentries = 1ull << o->global_cache_log2;
   }
+  const uint32_t warp_log2 = o->warp_cache_log2 == 0xFFFFFFFFu ? (gentries ? 0u : 9u) : o->warp_cache_log2;
   const uint64_t off_ctl = 0;
   const uint64_t off_blob = align256(sizeof(gx::Ctl));
   const uint64_t off_front = align256(off_blob + 4ull * net.blob.size());
@@ -191,8 +194,8 @@ gx_status gx_explore_noalloc(const gx_net* h, const gx_explore_opts* opts, void*
   if (ea.stage) smem += blob_bytes;
   // the per-warp cache of seen vectors lives in shared memory: same rule as gx_explore
   ea.cache_log2 = 0;
-  if (o->warp_cache_log2) {
-    ea.cache_log2 = o->warp_cache_log2 == 0xFFFFFFFFu ? 9 : (int)o->warp_cache_log2;
+  if (warp_log2) {
+    ea.cache_log2 = (int)warp_log2;
     if (ea.cache_log2 > 12) return gx::fail(GX_ERR_INVALID, "warp_cache_log2 must be at most 12");
     if (W == 4) ea.cache_log2 -= 1;  // 16-byte entries: the same bytes as 2^n 2-word ones
     smem += 4ull * W * (gx::kBlock / 32) * (1ull << ea.cache_log2);

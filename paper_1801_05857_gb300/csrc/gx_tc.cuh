@@ -2,9 +2,10 @@
 // cores): both layers of the MLP as tcgen05.mma BF16 x BF16 -> FP32 products
 // with the accumulator in tensor memory (TMEM), 128 states per tile.
 //
-// One CTA of 128 threads; thread t owns row t of a tile (one state), which is
-// also TMEM lane t of the M = 128 accumulator, so every epilogue is
-// thread-local:
+// The scoring threads are warps 0-3 of their CTA (128 threads, which
+// synchronise among themselves on a named barrier, so a larger CTA may score
+// too); thread t owns row t of a tile (one state), which is also TMEM lane t
+// of the M = 128 accumulator, so every epilogue is thread-local:
 //
 //   X  (128 x 16 BF16)  = bf16(hist / sum(hist))      (fraction of processes per local state)
 //   A1 = X W1^T         -> TMEM columns [0, 128)      one MMA, K = 16
@@ -58,6 +59,27 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
 }
 
 __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// The scoring threads (warps 0-3 of the CTA, TMEM lanes 0-127) synchronise on
+// named barrier 1 among themselves, so a larger CTA whose other warps do
+// something else can score tiles too.
+constexpr int kTcBarrier = 1;
+__device__ __forceinline__ void tc_sync() {
+  asm volatile("bar.sync %0, %1;" ::"n"(kTcBarrier), "n"(kRows) : "memory");
+}
+// OR of pred over the scoring threads, in every one of them.
+__device__ __forceinline__ int tc_sync_or(int pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.b32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.b32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(pred), "n"(kTcBarrier), "n"(kRows)
+      : "memory");
+  return r;
+}
 
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_slot, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_slot), "r"(ncols)
@@ -276,17 +298,17 @@ __device__ __forceinline__ TcScorer tc_setup(void* dyn, const TcWeights* __restr
     tmem_relinquish();
   }
   tc_fence_before();
-  __syncthreads();
+  tc_sync();
   tc_fence_after();
   bool ok = mbar_wait_bounded(saddr(&s->mbar_load), 0);
   if (!ok) ok = mbar_wait_bounded(saddr(&s->mbar_load), 0);  // the copy must land before the CTA leaves
-  const int bad = __syncthreads_or(!ok);
+  const int bad = tc_sync_or(!ok);
   return TcScorer{s, s->tmem_slot, 0u, bad == 0};
 }
 
 __device__ __forceinline__ void tc_teardown(const TcScorer& sc) {
   tc_fence_before();
-  __syncthreads();
+  tc_sync();
   if (threadIdx.x < 32) {
     tc_fence_after();
     tmem_dealloc(sc.tmem, kTmemCols);
@@ -297,7 +319,7 @@ __device__ __forceinline__ void tc_teardown(const TcScorer& sc) {
 __device__ __forceinline__ bool tc_wait(TcScorer& sc) {
   const bool ok = mbar_wait_bounded(saddr(&sc.s->mbar), sc.phase);
   sc.phase ^= 1u;
-  const int bad = __syncthreads_or(!ok);
+  const int bad = tc_sync_or(!ok);
   tc_fence_after();
   return bad == 0;
 }
@@ -325,7 +347,7 @@ __device__ __forceinline__ bool tc_score_tile(TcScorer& sc, const uint32_t (&hw)
     *reinterpret_cast<uint4*>(s->x + core_offset(t, 8, 2)) = make_uint4(q[4], q[5], q[6], q[7]);
   }
   fence_async_smem();
-  __syncthreads();
+  tc_sync();
   if (t == 0) {
     tc_fence_after();
     mma_bf16(sc.tmem, smem_desc(saddr(s->x), 128, 256), smem_desc(saddr(s->wt.w1), 128, 256), 0u);
@@ -350,7 +372,7 @@ __device__ __forceinline__ bool tc_score_tile(TcScorer& sc, const uint32_t (&hw)
   }
   tc_fence_before();
   fence_async_smem();
-  __syncthreads();
+  tc_sync();
   if (t == 0) {
     tc_fence_after();
     const uint32_t ha = saddr(s->h), wa = saddr(s->wt.w2);
@@ -372,7 +394,7 @@ __device__ __forceinline__ bool tc_score_tile(TcScorer& sc, const uint32_t (&hw)
   y = acc_y;
   // our TMEM reads and the tile's shared-memory use end before the next tile starts
   tc_fence_before();
-  __syncthreads();
+  tc_sync();
   return true;
 }
 

@@ -56,7 +56,8 @@ class gx_explore_opts(ctypes.Structure):
                 ("partition_min_states", u32), ("guided_bins", u32), ("warp_cache_log2", u32),
                 ("guided_scale", ctypes.c_float), ("watch", u32), ("watch_proc", u32),
                 ("watch_state", u32), ("stop_at_first_violation", u32), ("violation_cap", u32),
-                ("host_loop", u32), ("region_passes", u32), ("global_cache_log2", u32)]
+                ("host_loop", u32), ("region_passes", u32), ("global_cache_log2", u32),
+                ("guided_fused", u32)]
 
 
 MLP_IN, MLP_HIDDEN = 16, 128

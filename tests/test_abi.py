@@ -85,7 +85,9 @@ def test_stats_before_search_is_a_state_error():
 
 def test_default_opts_values():
     o = gx.default_opts()
-    assert (o.bucket_words, o.hash_rounds, o.deadlock_cap, o.warp_cache_log2) == (8, 8, 1024, 9)
+    assert (o.bucket_words, o.hash_rounds, o.deadlock_cap) == (8, 8, 1024)
+    # both caches of seen vectors automatic; region passes automatic; scoring in its own kernel
+    assert (o.warp_cache_log2, o.global_cache_log2, o.region_passes, o.guided_fused) == (0xFFFFFFFF, 0xFFFFFFFF, 0, 0)
 
 
 def test_binding_constants_match_the_header():

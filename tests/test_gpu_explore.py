@@ -434,3 +434,37 @@ def test_global_cache_is_cleared_between_searches(cuda):
         r = oracle.explore(net)
         s = gx.stats(h)
         assert (s["states"], s["transitions"], gx.levels(h)) == (r.states, r.transitions, r.levels)
+
+
+@pytest.mark.parametrize("bucket,passes", [(16, 1), (8, 2), (32, 4)])
+def test_large_irregular_network_against_stored_oracle(cuda, bucket, passes):
+    """16 processes x 16 local states (3-word vectors in 4-word slots), 3-party rules
+    on 10 % of the labels that shape the reachable set (1.08e8 states, 3.5 times as
+    many as without the rule edges): states, transitions, every level, the deadlock
+    digest and the digest of the whole set equal the oracle's, written by
+    tests/golden/make_golden.py; with one, two and four region passes."""
+    g = _golden_case("large3_network.json")
+    net = inputs.random_network(**g["generator"])
+    h, s, lv, ws = run_gpu(net, table_bytes=4 << 30, bucket_words=bucket, hash_rounds=32, region_passes=passes)
+    assert s["slot_words"] == 4 and s["region_passes"] == passes
+    assert (s["states"], s["transitions"]) == (g["states"], g["transitions"])
+    assert lv == g["levels"]
+    assert (s["deadlock_count"], s["deadlock_sum"], s["deadlock_xor"]) == (
+        g["deadlock_count"], g["deadlock_sum"], g["deadlock_xor"])
+    assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])
+    assert s["fill"] <= 0.75
+
+
+@pytest.mark.parametrize("host_loop", [1, 0])
+def test_global_cache_with_multi_lane_groups_on_the_mid_network(cuda, host_loop):
+    """The GPU-wide cache forced on with 16 lanes per 32-word bucket on the mid network
+    (62M states): one lane of each group reads the cache and the group takes its
+    answer, so a concurrent write by another warp cannot split the group before
+    find-or-put's group-wide votes.  Exact against the stored oracle values."""
+    g = _golden_case("mid_network.json")
+    net = inputs.random_network(**g["generator"])
+    h, s, lv, ws = run_gpu(net, table_bytes=4 << 28, bucket_words=32, hash_rounds=32, global_cache_log2=23,
+                           host_loop=host_loop)
+    assert s["group_lanes"] == 16 and s["global_cache_entries"] == 1 << 23
+    assert (s["states"], s["transitions"], lv) == (g["states"], g["transitions"], g["levels"])
+    assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])

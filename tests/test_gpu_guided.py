@@ -163,11 +163,12 @@ def _bfs_first(net):
     return n, gx.stats(h)
 
 
+@pytest.mark.parametrize("fused", [0, 1], ids=["split", "fused"])
 @pytest.mark.parametrize("seed,n_procs,k", [(10, 9, 1), (11, 10, 3), (12, 12, 2)])
-def test_guided_search_finds_a_replayable_deadlock_faster_than_bfs(cuda, seed, n_procs, k):
+def test_guided_search_finds_a_replayable_deadlock_faster_than_bfs(cuda, seed, n_procs, k, fused):
     params, _ = _trained()
     net = inputs.planted_network(seed, n_procs, n_traps=k)
-    h, n, found, s = _guided(net, params)
+    h, n, found, s = _guided(net, params, guided_fused=fused)
     assert n == 1 and s["deadlock_count"] == 1
     trace = gx.guided_trace(h)
     _replay(net, trace)
@@ -189,30 +190,33 @@ def test_trained_network_beats_untrained(cuda):
     assert s1["explored"] < s2["explored"]
 
 
-def test_guided_search_without_deadlock_is_exhaustive(cuda):
+@pytest.mark.parametrize("fused", [0, 1], ids=["split", "fused"])
+def test_guided_search_without_deadlock_is_exhaustive(cuda, fused):
     params, _ = _trained(100)
     net = inputs.token_ring(8)
-    h, n, found, s = _guided(net, params, guided_batch=256)
+    h, n, found, s = _guided(net, params, guided_batch=256, guided_fused=fused)
     assert n == 0 and s["complete"] == 1 and s["deadlock_count"] == 0
     r = oracle.explore(net)
     assert s["states"] == r.states and s["explored"] == r.states
     assert s["transitions"] == r.transitions
 
 
+@pytest.mark.parametrize("fused", [0, 1], ids=["split", "fused"])
 @pytest.mark.parametrize("host_loop", [0, 1])
-def test_device_and_host_iteration_loops(cuda, host_loop):
+def test_device_and_host_iteration_loops(cuda, host_loop, fused):
     """The guided search runs as one graph (device loop) or one host round trip
-    per iteration; both find a replayable deadlock, and both are exhaustive on a
-    network without one."""
+    per iteration, with the scoring in its own kernel or inside the expansion;
+    each finds a replayable deadlock, and each is exhaustive on a network
+    without one."""
     params, _ = _trained(200)
     net = inputs.planted_network(10, 9, n_traps=1)
-    h, n, found, s = _guided(net, params, host_loop=host_loop)
+    h, n, found, s = _guided(net, params, host_loop=host_loop, guided_fused=fused)
     assert n == 1 and s["deadlock_count"] == 1
     trace = gx.guided_trace(h)
     _replay(net, trace)
     assert list(found[0]) == list(trace[-1])
     ring = inputs.token_ring(7)
-    _, n2, _, s2 = _guided(ring, params, host_loop=host_loop, guided_batch=512)
+    _, n2, _, s2 = _guided(ring, params, host_loop=host_loop, guided_batch=512, guided_fused=fused)
     r = oracle.explore(ring)
     assert n2 == 0 and s2["complete"] == 1 and (s2["states"], s2["transitions"]) == (r.states, r.transitions)
 
