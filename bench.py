@@ -224,11 +224,12 @@ def ncu_traffic(args, s: dict, probes: int, launches: int) -> dict | None:
     src = b"".join(open(os.path.join(ROOT, p), "rb").read() for p in t["kernel_sources"])
     if hashlib.sha256(src).hexdigest() != t["kernel_sources_sha256"]:
         return None
-    if cfg.get("table_log2_words") == args.table_log2_words and cfg.get("region_passes", 1) == s["region_passes"]:
+    if "dram_bytes_per_search" in t and cfg.get("table_log2_words") == args.table_log2_words \
+            and cfg.get("region_passes", 1) == s["region_passes"]:
         return {"dram_bytes_per_launch": int(t["dram_bytes_per_search"] // max(launches, 1)),
                 "source": f"profiles/{os.path.basename(path)}: ncu dram__bytes_read.sum + dram__bytes_write.sum "
                           "of the same configuration, per launch"}
-    ratio = t["dram_bytes_per_search"] / t["algorithmic_bytes_per_search"]
+    ratio = t["dram_bytes_captured"] / t["algorithmic_bytes_captured"]
     alg = algorithmic_bytes(dict(s, probes=probes))
     return {"dram_bytes_per_launch": int(ratio * alg / max(launches, 1)),
             "source": f"profiles/{os.path.basename(path)}: ncu dram__bytes_read.sum + dram__bytes_write.sum "
@@ -528,6 +529,7 @@ def guided_part(torch, gx, inputs, guide) -> dict:
     lo = losses.cpu().numpy()
     return {"train": {"networks": len(train_nets), "examples": int(hist.shape[0]),
                       "label_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3), "steps": 4000, "lr": 1e-3,
+                      "ms_per_adam_step": round((t2 - t1) * 1e3 / 4000, 4), "batch": 1024,
                       "loss_first": round(float(lo[:10].mean()), 4), "loss_last": round(float(lo[-50:].mean()), 4)},
             "scoring": scoring_rate(torch, gx, params),
             "summary": summary, "instances": rows}

@@ -394,9 +394,15 @@ gx_status gx_mlp_forward(const float* params, const uint8_t* hist, uint64_t n, f
 gx_status gx_wait_selftest(uint32_t spin_limit, void* stream);
 
 /* Gradient of the mean squared error over n examples at params (grad: device,
- * GX_MLP_PARAMS floats, overwritten; loss: device, one float).  The result
- * does not depend on scheduling (partial gradients summed in a fixed order);
- * scratch for them is allocated on `stream` and freed before returning. */
+ * GX_MLP_PARAMS floats, overwritten; loss: device, one float), on the tensor
+ * cores: per tile of 128 examples the forward pass, then the backward products
+ * D2 W2, D2^T [h1 | 1] and DA1^T [x | 1] as tcgen05 MMAs (D2 and DA1, the
+ * backward signals of the two layers, enter them rounded to BF16; the bias
+ * gradients come from the ones columns), accumulated in TMEM.  The result does
+ * not depend on scheduling (each CTA sums its tiles in order, the partial
+ * gradients are summed in a fixed order); scratch for them is allocated on
+ * `stream` and freed before returning.  Synchronises `stream`;
+ * GX_ERR_SPIN_LIMIT if a wait for a tensor-core product timed out. */
 gx_status gx_mlp_grad(const float* params, const uint8_t* hist, const float* label, uint64_t n,
                       float* grad, float* loss, void* stream);
 

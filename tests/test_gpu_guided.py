@@ -62,6 +62,26 @@ def test_mlp_forward_and_gradient_match_float64(cuda):
     assert np.max(np.abs(g - gr)) <= 1e-3 * np.max(np.abs(gr)) + 1e-7
 
 
+@pytest.mark.parametrize("n", [1, 127, 128, 129, 1000, 256 * 128 + 300])
+def test_tensor_core_gradient_tiles_match_float64(cuda, n):
+    """The gradient on the tensor cores, one 128-example tile per product: a single
+    example, ragged tails, and more tiles than CTAs (256 at most), so that a CTA
+    accumulates several tiles in TMEM.  Against the float64 gradient of the kernels'
+    arithmetic model within 1e-3 of its largest entry; the loss within 1e-4."""
+    import torch
+    p = torch.empty(gx.MLP_PARAMS, dtype=torch.float32, device="cuda")
+    gx.mlp_init(p, 11)
+    rng = np.random.default_rng(n)
+    hist_np = rng.multinomial(10, np.ones(16) / 16, size=n).astype(np.uint8)
+    label_np = rng.random(n).astype(np.float32)
+    g, loss = gx.mlp_grad(p, torch.from_numpy(hist_np).cuda(), torch.from_numpy(label_np).cuda())
+    lr_, gr = omlp.loss_and_grad(p.cpu().numpy(), hist_np, label_np)
+    g = g.cpu().numpy()
+    assert np.isfinite(g).all()
+    assert abs(float(loss.item()) - lr_) <= 1e-4 * lr_ + 1e-7
+    assert np.max(np.abs(g - gr)) <= 1e-3 * np.max(np.abs(gr)) + 1e-7
+
+
 @pytest.mark.parametrize("n", [1, 127, 128, 129, 4099, 152 * 4 * 128 * 2 + 77])
 def test_tensor_core_forward_tiles_match_float64(cuda, n):
     """gx_mlp_forward scores 128 states per tile on the tensor cores; ragged
