@@ -203,20 +203,24 @@ typedef struct gx_explore_opts {
                                     (address-translation reach).  Results do not depend on
                                     it.  0 = auto: the fewest passes whose regions are at
                                     most 64 GiB (1 for tables up to 64 GiB) */
-  uint32_t global_cache_log2;    /* GPU-wide cache of recently seen vectors (1- and 2-word
-                                    vectors; no effect on 4-word ones): 2^n direct-mapped
-                                    64-bit entries in the workspace, cleared at the start of
-                                    each search and small enough to stay in L2.  A vector
-                                    goes in after its find-or-put found or inserted it, so a
-                                    hit is a known state and skips the table probe; most
-                                    successors of a level lead into the levels just before
-                                    and after it.  0 = off, 1..26 = 2^n, 0xFFFFFFFF =
-                                    automatic (gx_default_opts): 2^23 entries (64 MiB) for
-                                    1- and 2-word vectors in tables of at least 2^26 slots
-                                    with one lane per bucket (group_lanes 1), else off.  Mid network: 0.36 bucket reads per successor
-                                    and 18.9 ms, against 0.82 and 20.4 ms with the per-warp
-                                    cache; small sizes (2^14-2^18) are far slower, many warps
-                                    writing the same few lines */
+  uint32_t global_cache_log2;    /* GPU-wide cache of recently seen vectors: 2^n
+                                    direct-mapped 64-bit entries in the workspace, cleared at
+                                    the start of each search and small enough to stay in L2.
+                                    An entry holds a vector exactly: 1- and 2-word vectors
+                                    as they are, 4-word vectors as their field bits packed
+                                    into 64 (no effect on 4-word vectors whose fields take
+                                    more than 64 bits).  A vector goes in after its
+                                    find-or-put found or inserted it, so a hit is a known
+                                    state and skips the table probe; most successors of a
+                                    level lead into the levels just before and after it.
+                                    0 = off, 1..26 = 2^n, 0xFFFFFFFF = automatic
+                                    (gx_default_opts): 2^23 entries (64 MiB) for 1- and
+                                    2-word vectors in tables of at least 2^26 slots with one
+                                    lane per bucket (group_lanes 1), else off.  Mid network:
+                                    0.36 bucket reads per successor and 18.9 ms, against 0.82
+                                    and 20.4 ms with the per-warp cache; small sizes
+                                    (2^14-2^18) are far slower, many warps writing the same
+                                    few lines */
   uint32_t guided_fused;         /* GX_DL_GUIDED: 1 = score the states an iteration inserts
                                     inside its expansion kernel (each CTA keeps them in shared
                                     memory and scores 128 at a time on the tensor cores), 0 =

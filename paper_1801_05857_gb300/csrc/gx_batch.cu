@@ -221,6 +221,7 @@ struct SmemTarget {
   __device__ __forceinline__ uint64_t region_bits() const { return 0; }
   __device__ __forceinline__ unsigned long long* gcache() const { return nullptr; }
   __device__ __forceinline__ uint64_t gcache_mask() const { return 0; }
+  __device__ __forceinline__ GKey gkey() const { return GKey{{64u, 64u, 64u}}; }
 };
 
 // The batched kernel keeps a network index and chunk bounds besides the

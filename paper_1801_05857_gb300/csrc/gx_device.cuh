@@ -63,6 +63,26 @@ __device__ __forceinline__ uint64_t bucket_of(uint64_t h, uint64_t mul, int log2
   return (h * mul) >> (64 - log2nb);
 }
 
+// Span of the later hash rounds: 2^kSpanLog2Bytes bytes of table (64 GiB).
+// Random reads run at the full rate inside any 64 GiB of device memory and
+// about 4x slower across 128 GiB (the reach of the GPU's address translation),
+// so in a larger table every round after the first stays inside the 64 GiB
+// span that round 0 picked: the top bits of the bucket come from round 0, the
+// rest from the round's own multiplier.  Tables of at most 64 GiB are not
+// affected.  A region pass that takes the successors of one span (or part of
+// one) then reads nothing outside it, in any round.
+constexpr int kSpanLog2Bytes = 36;
+
+// Bucket of round k >= 1 for a table of 2^log2nb buckets of B words, given
+// round 0's bucket b0.
+template <int B>
+__device__ __forceinline__ uint64_t bucket_in_span(uint64_t h, uint64_t mul, int log2nb, uint64_t b0) {
+  static_assert(B >= 1 && B <= 64 && (B & (B - 1)) == 0, "bucket words: a power of two up to 64");
+  constexpr int kSpanLog2 = kSpanLog2Bytes - 2 - (B >= 2) - (B >= 4) - (B >= 8) - (B >= 16) - (B >= 32) - (B >= 64);
+  if (log2nb <= kSpanLog2) return bucket_of(h, mul, log2nb);
+  return ((b0 >> kSpanLog2) << kSpanLog2) | bucket_of(h, mul, kSpanLog2);
+}
+
 // ---- loads that bypass L1 (the table is shared by all SMs; slots only ever
 // go from empty to one final value, so a stale copy is never wrong, but L1
 // allocation is pure overhead for random probes).
@@ -171,8 +191,9 @@ __device__ __forceinline__ int find_or_put_hashed(uint32_t* __restrict__ table, 
   static_assert(S >= 1 && S % G == 0, "group size must divide the slots per bucket");
   constexpr int SPL = S / G;
   constexpr int LW = SPL * W;
+  const uint64_t b0 = bucket_of(h, muls[0], log2nb);
   for (int k = 0; k < rounds; ++k) {
-    const uint64_t b = bucket_of(h, muls[k], log2nb);
+    const uint64_t b = k == 0 ? b0 : bucket_in_span<B>(h, muls[k], log2nb, b0);
     uint32_t* lane_slots = table + b * (uint64_t)B + (uint64_t)g.glane * LW;
     uint32_t s[LW];
     if (PRE && k == 0) {

@@ -199,8 +199,9 @@ inline int ilog2(uint64_t x) {
 constexpr int kPartCtas = 1024;  // CTAs of the partitioned count/scatter passes (at most)
 // Largest table region one pass of the direct path probes by default: random
 // 32-byte reads run at the full rate over any 64 GiB of a table and 4x slower
-// over 128 GiB (the GPU's address-translation reach).
-constexpr uint64_t kAutoRegionBytes = 64ull << 30;
+// over 128 GiB (the GPU's address-translation reach); the later hash rounds of
+// a vector stay inside the same 64 GiB span as its first (bucket_in_span).
+constexpr uint64_t kAutoRegionBytes = 1ull << gxd::kSpanLog2Bytes;
 constexpr uint32_t kAutoCache = 0xFFFFFFFFu;  // warp_cache_log2 / global_cache_log2: automatic
 
 // Arguments of pass q of `passes` region passes over a table of 2^log2nb buckets.
@@ -226,11 +227,15 @@ struct Plan {
   uint64_t part_min = 0;   // smallest level that may use the partitioned path
   uint32_t regions = 1;    // passes per level of the direct path (region passes)
   uint64_t gcache = 0;     // entries of the GPU-wide cache of seen vectors (0 = off)
+  uint32_t gkey[3] = {64, 64, 64};  // key offsets of words 1..3 (4-word vectors)
   uint32_t warp_log2 = 0;  // per-warp cache of seen vectors: 2^warp_log2 entries (0 = off)
   uint64_t off_ctl = 0, off_blob = 0, off_dl = 0, off_viol = 0, off_loop = 0, off_front = 0, off_table = 0;
   uint64_t off_hist = 0, off_off = 0, off_ptot = 0, off_tot = 0, off_succ = 0, off_gcache = 0;
   uint64_t total = 0;
   const KernelSet* ks = nullptr;
+  // the level kernel: ks->expand, or the queued second kernel with region passes
+  cudaError_t (*expand)(const ExpandArgs&, int, size_t, cudaStream_t) = nullptr;
+  const void* expand_fn = nullptr;
 };
 
 gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
@@ -289,16 +294,25 @@ gx_status make_plan(const Net& net, const gx_explore_opts* o, Plan& P) {
     while (P.regions < 16 && tbytes / P.regions > kAutoRegionBytes) P.regions *= 2;
   }
   if (P.regions > P.nb) P.regions = (uint32_t)P.nb;
+  // with region passes most generated successors fall outside the pass's region:
+  // the queued kernel (where it is a second one) probes only those inside it, 32 at a time
+  const bool queued = P.regions > 1 && P.ks->expand_queued;
+  P.expand = queued ? P.ks->expand_queued : P.ks->expand;
+  P.expand_fn = queued ? P.ks->expand_queued_fn : P.ks->expand_fn;
   // the caches of seen vectors: auto = the GPU-wide one (2^23 entries) for 1- and
   // 2-word vectors in tables of at least 2^26 slots with one lane per bucket (where it
   // was measured), else the per-warp one (2^9)
+  // (4-word vectors use it only when their fields fit one 64-bit key)
+  const bool key_fits = P.W <= 2 || gx::cache_key_shifts(net, P.gkey);
   if (o->global_cache_log2 == kAutoCache) {
     if (P.W <= 2 && P.G == 1 && slots >= (1ull << 26)) P.gcache = 1ull << 23;
   } else if (o->global_cache_log2) {
     if (o->global_cache_log2 > 26) return fail(GX_ERR_INVALID, "global_cache_log2 must be at most 26");
-    if (P.W <= 2) P.gcache = 1ull << o->global_cache_log2;  // 4-word vectors: not used
+    if (key_fits) P.gcache = 1ull << o->global_cache_log2;
   }
-  P.warp_log2 = o->warp_cache_log2 == kAutoCache ? (P.gcache ? 0u : 9u) : o->warp_cache_log2;
+  // (the queued 4-word kernel: 2^6, whose 4 KiB per CTA leave room for 5 CTAs per SM;
+  // 2^9 took 4.55 s on the memory-scaled network, 2^6 3.52 s)
+  P.warp_log2 = o->warp_cache_log2 == kAutoCache ? (P.gcache ? 0u : queued ? 6u : 9u) : o->warp_cache_log2;
   P.cs = o->successor_buffer ? o->successor_buffer : std::min<uint64_t>(slots / 2, (1ull << 32) - 1);
   if (P.logp == 0) P.cs = 0;  // partitioned path off: no buffer
   if (P.cs >= (1ull << 32)) return fail(GX_ERR_INVALID, "successor_buffer must be below 2^32 vectors");
@@ -434,7 +448,7 @@ gx_status build_loop_graph(gx_net* h, const Plan& P, Ctl* ctl, uint32_t* table, 
   cudaGraphNode_t cnode;
   GX_CUDA(cudaGraphAddNode(&cnode, g, &start, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  GX_CUDA(add_kernel(body, nullptr, 0, P.ks->expand_fn, dim3((unsigned)grid), dim3(kBlock), smem, args_e, &ex));
+  GX_CUDA(add_kernel(body, nullptr, 0, P.expand_fn, dim3((unsigned)grid), dim3(kBlock), smem, args_e, &ex));
   // region passes after the first: clear the claim counter, expand again
   for (uint32_t q = 1; q < P.regions; ++q) {
     ExpandArgs eq = region_pass(eg, P.regions, q);
@@ -447,7 +461,7 @@ gx_status build_loop_graph(gx_net* h, const Plan& P, Ctl* ctl, uint32_t* table, 
     mp.height = 1;
     cudaGraphNode_t mz, exq;
     GX_CUDA(cudaGraphAddMemsetNode(&mz, body, &ex, 1, &mp));
-    GX_CUDA(add_kernel(body, &mz, 1, P.ks->expand_fn, dim3((unsigned)grid), dim3(kBlock), smem, args_q, &exq));
+    GX_CUDA(add_kernel(body, &mz, 1, P.expand_fn, dim3((unsigned)grid), dim3(kBlock), smem, args_q, &exq));
     ex = exq;
   }
   GX_CUDA(add_kernel(body, &ex, 1, reinterpret_cast<const void*>(&gxd::level_advance_kernel), dim3(1), dim3(1), 0,
@@ -552,6 +566,7 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
   ea.count_states = 1;  // region passes set their own (region_pass)
   ea.gcache = gcache;
   ea.gcache_mask = P.gcache ? P.gcache - 1 : 0;
+  for (int w = 0; w < 3; ++w) ea.gkey_shift[w] = P.gkey[w];
   uint32_t* viol = reinterpret_cast<uint32_t*>(base + P.off_viol);
   if (o->watch) {
     const uint32_t wp = o->watch_proc;
@@ -578,9 +593,9 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
                                       std::to_string(smem) + " bytes of shared memory per CTA, more than " +
                                       std::to_string(dev.smem_optin));
   }
-  GX_CUDA(cudaFuncSetAttribute(P.ks->expand_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GX_CUDA(cudaFuncSetAttribute(P.expand_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  GX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.ks->expand_fn, kBlock, smem));
+  GX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, P.expand_fn, kBlock, smem));
   if (per_sm < 1) return fail(GX_ERR_INVALID, "expansion kernel does not fit on an SM");
   if (o->ctas_per_sm) per_sm = std::min<int>(per_sm, (int)o->ctas_per_sm);
   const uint64_t max_grid = (uint64_t)dev.sms * per_sm;
@@ -714,7 +729,7 @@ gx_status run_search(gx_net* h, const gx_explore_opts* opts, bool stop_first, vo
       const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, max_grid));
       for (uint32_t q = 0; q < P.regions; ++q) {
         GX_CUDA(cudaMemsetAsync(&ctl->claim, 0, sizeof(unsigned long long), st));
-        GX_CUDA(P.ks->expand(region_pass(ea, P.regions, q), grid, smem, st));
+        GX_CUDA(P.expand(region_pass(ea, P.regions, q), grid, smem, st));
         ++launches;
       }
     }

@@ -95,8 +95,9 @@ __device__ __forceinline__ int64_t find_slot(const uint32_t* __restrict__ table,
                                              const uint64_t* __restrict__ muls, const uint32_t (&v)[W]) {
   constexpr int S = B / W;
   const uint64_t h = vec_hash<W>(v);
+  const uint64_t b0 = bucket_of(h, muls[0], log2nb);
   for (int k = 0; k < rounds; ++k) {
-    const uint64_t b = bucket_of(h, muls[k], log2nb);
+    const uint64_t b = k == 0 ? b0 : bucket_in_span<B>(h, muls[k], log2nb, b0);
     uint32_t s[B];
     load_words<B>(table + b * (uint64_t)B, s);
 #pragma unroll

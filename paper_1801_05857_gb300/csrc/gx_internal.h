@@ -52,6 +52,25 @@ struct Net {
   uint32_t init_vec[kMaxWords] = {0, 0, 0, 0};
 };
 
+// Bit offsets of words 1..3 in the 64-bit key that the GPU-wide cache of seen
+// vectors stores for a vector: each word's payload (its fields sit at the low
+// bits of the word) follows the previous word's, and a word without fields gets
+// 64 (left out).  Returns false when the fields take more than 64 bits in all,
+// so that no such key exists.
+inline bool cache_key_shifts(const Net& n, uint32_t (&s)[3]) {
+  uint32_t used[kMaxWords] = {0, 0, 0, 0};
+  for (uint32_t p = 0; p < n.n_procs; ++p) {
+    const uint32_t end = n.field_shift[p] + n.field_bits[p];
+    if (end > used[n.field_word[p]]) used[n.field_word[p]] = end;
+  }
+  uint32_t off = used[0];
+  for (int w = 1; w < 4; ++w) {
+    s[w - 1] = used[w] ? off : 64u;
+    off += used[w];
+  }
+  return off <= 64;
+}
+
 }  // namespace gx
 
 // The opaque handle: the encoded network plus the results of the last search.

@@ -240,6 +240,11 @@ __device__ __forceinline__ const uint32_t* stage_tables(uint32_t* sm, const gx::
   return s_tab;
 }
 
+// Offsets in a 64-bit key of the payload of words 1..3 (ExpandArgs.gkey_shift).
+struct GKey {
+  uint32_t s[3];
+};
+
 // Where find-or-put inserts and where new vectors go: one network's table and
 // frontier ring (the level being expanded starts at begin()).  Target holds
 // the values (the batched kernel loads them per network); ParamTarget reads
@@ -263,6 +268,7 @@ struct Target {
   __device__ __forceinline__ uint64_t region_bits() const { return 0; }
   __device__ __forceinline__ unsigned long long* gcache() const { return nullptr; }
   __device__ __forceinline__ uint64_t gcache_mask() const { return 0; }
+  __device__ __forceinline__ GKey gkey() const { return GKey{{64u, 64u, 64u}}; }
 };
 
 struct ParamTarget {
@@ -279,6 +285,7 @@ struct ParamTarget {
   __device__ __forceinline__ uint64_t region_bits() const { return a.region_bits; }
   __device__ __forceinline__ unsigned long long* gcache() const { return a.gcache; }
   __device__ __forceinline__ uint64_t gcache_mask() const { return a.gcache_mask; }
+  __device__ __forceinline__ GKey gkey() const { return GKey{{a.gkey_shift[0], a.gkey_shift[1], a.gkey_shift[2]}}; }
 };
 
 // Per-warp staging of new vectors in shared memory: lanes that inserted a
@@ -384,18 +391,34 @@ struct WarpCache {
 // the levels just before and after it, which were inserted or looked up
 // moments earlier by some warp of the GPU.
 template <int W>
-__device__ __forceinline__ unsigned long long gcache_key(const uint32_t (&v)[W]) {
-  if constexpr (W == 1) return (unsigned long long)v[0];
-  else return (unsigned long long)v[0] | ((unsigned long long)v[W > 1 ? 1 : 0] << 32);
+__device__ __forceinline__ unsigned long long gcache_key(const uint32_t (&v)[W], const GKey& k) {
+  if constexpr (W == 1) {
+    return (unsigned long long)v[0];
+  } else if constexpr (W == 2) {
+    return (unsigned long long)v[0] | ((unsigned long long)v[1] << 32);
+  } else {
+    // the payload bits of the words side by side (fields sit at the low bits of
+    // each word, so the words' payloads do not overlap): one key per vector
+    unsigned long long key = v[0] & ~kTag;
+#pragma unroll
+    for (int w = 1; w < W; ++w)
+      if (k.s[w - 1] < 64) key |= (unsigned long long)(v[w] & ~kTag) << k.s[w - 1];
+    return key;
+  }
 }
+// Keys of 1- and 2-word vectors carry the tag bits and are never 0 (an empty
+// entry); the one 4-word vector whose key is 0 is never cached.
 template <int W>
 __device__ __forceinline__ bool gcache_hit(const unsigned long long* c, uint64_t mask, uint64_t h,
-                                           const uint32_t (&v)[W]) {
-  return __ldcg(c + ((h >> 32) & mask)) == gcache_key<W>(v);
+                                           const uint32_t (&v)[W], const GKey& k) {
+  const unsigned long long key = gcache_key<W>(v, k);
+  return (W <= 2 || key != 0ull) && __ldcg(c + ((h >> 32) & mask)) == key;
 }
 template <int W>
-__device__ __forceinline__ void gcache_put(unsigned long long* c, uint64_t mask, uint64_t h, const uint32_t (&v)[W]) {
-  __stcg(c + ((h >> 32) & mask), gcache_key<W>(v));
+__device__ __forceinline__ void gcache_put(unsigned long long* c, uint64_t mask, uint64_t h, const uint32_t (&v)[W],
+                                           const GKey& k) {
+  const unsigned long long key = gcache_key<W>(v, k);
+  if (W <= 2 || key != 0ull) __stcg(c + ((h >> 32) & mask), key);
 }
 
 // Successors each lane generates per round.  insert_lanes takes K per lane
@@ -445,7 +468,7 @@ __device__ __forceinline__ void insert_lanes(const T& a, const uint64_t* muls,
         // vectors that went to find-or-put)
         if ((b & a.region_mask()) != a.region_bits()) {
           hv[j] = false;
-        } else if (cache.base || (W <= 2 && a.gcache())) {
+        } else if (cache.base || a.gcache()) {
           // A vector this warp has already sent to find-or-put needs no second lookup,
           // nor does one that any warp found or inserted moments ago.  One lane of the
           // group reads (and writes) the caches and the group takes its answer: other
@@ -455,7 +478,7 @@ __device__ __forceinline__ void insert_lanes(const T& a, const uint64_t* muls,
           int known = 0;
           if (g.glane == 0)
             known = (cache.base && cache.template seen<W>(hh, x[j])) ||
-                    (W <= 2 && a.gcache() && gcache_hit<W>(a.gcache(), a.gcache_mask(), hh, x[j]));
+                    (a.gcache() && gcache_hit<W>(a.gcache(), a.gcache_mask(), hh, x[j], a.gkey()));
           if (g.template bcast<int>(known, g.base)) hv[j] = false;
         }
         if (hv[j]) {
@@ -471,8 +494,8 @@ __device__ __forceinline__ void insert_lanes(const T& a, const uint64_t* muls,
       const int r = find_or_put_from<W, B, G, true>(a.table(), a.log2nb(), a.rounds(), muls, x[j], g, probes,
                                                     pre[j]);
       if (r == FOP_FULL) err |= gx::ERR_TABLE_FULL;
-      else if (W <= 2 && a.gcache() && g.glane == 0)
-        gcache_put<W>(a.gcache(), a.gcache_mask(), vec_hash<W>(x[j]), x[j]);
+      else if (a.gcache() && g.glane == 0)
+        gcache_put<W>(a.gcache(), a.gcache_mask(), vec_hash<W>(x[j]), x[j], a.gkey());
       if (g.glane == i / K && r == FOP_INSERTED) inserted[i % K] = true;
     }
   }
@@ -496,7 +519,7 @@ __device__ __forceinline__ void resolve_lanes(const T& a, const uint64_t* muls, 
     ++probes;
     const int r = find_or_put_hashed<W, B, 1, true>(a.table(), a.log2nb(), a.rounds(), muls, x, hh, g, probes, pre);
     if (r == FOP_FULL) err |= gx::ERR_TABLE_FULL;
-    else if (W <= 2 && a.gcache()) gcache_put<W>(a.gcache(), a.gcache_mask(), hh, x);
+    else if (a.gcache()) gcache_put<W>(a.gcache(), a.gcache_mask(), hh, x, a.gkey());
     inserted = r == FOP_INSERTED;
   }
   st.push<W>(a, inserted, x, err);
@@ -520,18 +543,29 @@ struct WarpQueue {
 
 // Resident CTAs per SM the level kernel is compiled for (register budget).
 // A lane holds min(G, 4) first buckets in flight of B / G words each; up to
-// 8 such words of 1- or 2-word slots fit 48 registers (5 CTAs), up to 16 fit
-// 64 (4 CTAs), more get 85 (3 CTAs); 4-word slots with 4 or more lanes per
-// bucket also get 3.  (Checked with -Xptxas -v: at most a few bytes spill.)
+// 8 such words fit 48 registers (5 CTAs), up to 16 fit 64 (4 CTAs), more get
+// 85 (3 CTAs); 4-word slots with 4 or more lanes per bucket also get 3.
+// (Checked with -Xptxas -v: at most a few bytes spill.  4-word slots in
+// 16-word buckets spill 48 bytes at 48 registers and ran slower there.)  The
+// level kernel is latency-bound, so the extra CTA pays: 4-word slots in 8-word
+// buckets explore the memory-scaled network in 4.49 s at 5 CTAs, 4.94 s at 4.
 template <int W, int B, int G>
 struct ExpandOcc {
   static constexpr int inflight = (G < 4 ? G : 4) * (B / G);
   static constexpr int min_ctas =
-      (W <= 2 && inflight <= 8) ? 5 : ((inflight <= 16 && !(W == 4 && G >= 4)) ? 4 : 3);
+      (inflight <= 8 && (W <= 2 || G == 1)) ? 5 : ((inflight <= 16 && !(W == 4 && G >= 4)) ? 4 : 3);
 };
 
-template <int W, int B, int G>
+// Q: the per-warp successor queue.  Generation rounds append the successors that
+// pass the filters (region, caches) to a queue in shared memory, and find-or-put
+// runs 32 queued successors at a time with every lane busy.  Built by default
+// for 1- and 2-word vectors with one lane per bucket; for 4-word vectors in 4-
+// and 8-word buckets it is a second kernel, chosen when region passes discard
+// most successors (memory-scaled network, 2 passes: 3.52 s queued against 4.48 s;
+// large3 network in 4 GiB, 1 pass: 57.8 ms queued against 49.4 ms).
+template <int W, int B, int G, bool Q = (G == 1 && W <= 2)>
 __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expand_kernel(const gx::ExpandArgs a) {
+  static_assert(!Q || G == 1, "the successor queue needs one lane per bucket");
   extern __shared__ __align__(16) uint32_t sm[];
   // the level being expanded: from the parameters, or (device-driven level
   // loop) from the control block the previous level's advance step wrote.
@@ -560,9 +594,10 @@ __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expa
   uint32_t probes = 0, err = 0;
   __shared__ uint32_t stage_mem[gx::kBlock / 32][kStage * W];
   WarpStage st{stage_mem[threadIdx.x >> 5], 0};
-  __shared__ uint32_t queue_mem[G == 1 ? gx::kBlock / 32 : 1][G == 1 ? kQueue * W : 1];
-  __shared__ unsigned long long queue_hash[G == 1 ? gx::kBlock / 32 : 1][G == 1 ? kQueue : 1];
-  WarpQueue<W> wq{queue_mem[G == 1 ? threadIdx.x >> 5 : 0], queue_hash[G == 1 ? threadIdx.x >> 5 : 0], 0};
+  constexpr bool kQueued = Q;
+  __shared__ uint32_t queue_mem[kQueued ? gx::kBlock / 32 : 1][kQueued ? kQueue * W : 1];
+  __shared__ unsigned long long queue_hash[kQueued ? gx::kBlock / 32 : 1][kQueued ? kQueue : 1];
+  WarpQueue<W> wq{queue_mem[kQueued ? threadIdx.x >> 5 : 0], queue_hash[kQueued ? threadIdx.x >> 5 : 0], 0};
   const ParamTarget tg{a, s_range};
   WarpCache cache{nullptr, 0};
   if (a.cache_log2 > 0) {
@@ -600,7 +635,7 @@ __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expa
     if (a.watch && acct) check_watch<W>(a, t, L, v);
     SuccIter it;
     it.init();
-    if constexpr (G == 1) {
+    if constexpr (kQueued) {
       while (__any_sync(FULLMASK, remaining != 0)) {
         uint32_t x[W];
         uint64_t hh = 0;
@@ -613,7 +648,7 @@ __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expa
           // the filters of insert_lanes: region, per-warp cache, GPU-wide cache
           if ((b & a.region_mask) != a.region_bits) keep = false;
           else if (cache.base && cache.template seen<W>(hh, x)) keep = false;
-          else if (W <= 2 && a.gcache && gcache_hit<W>(a.gcache, a.gcache_mask, hh, x)) keep = false;
+          else if (a.gcache && gcache_hit<W>(a.gcache, a.gcache_mask, hh, x, tg.gkey())) keep = false;
         }
         const uint32_t km = __ballot_sync(FULLMASK, keep);
         if (keep) {
@@ -659,7 +694,7 @@ __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expa
       }
     }
   }
-  if constexpr (G == 1) {  // what is left in the queue
+  if constexpr (kQueued) {  // what is left in the queue
     __syncwarp();
     const bool has = lane < wq.n;
     uint32_t y[W];
@@ -956,9 +991,9 @@ __global__ void __launch_bounds__(gx::kBlock) fop_kernel(const gx::FopArgs a) {
 
 namespace gx {
 
-template <int W, int B, int G>
+template <int W, int B, int G, bool Q = (G == 1 && W <= 2)>
 cudaError_t launch_expand(const ExpandArgs& a, int grid, size_t smem, cudaStream_t st) {
-  gxd::expand_kernel<W, B, G><<<grid, kBlock, smem, st>>>(a);
+  gxd::expand_kernel<W, B, G, Q><<<grid, kBlock, smem, st>>>(a);
   return cudaGetLastError();
 }
 template <int W, int B, int G>
@@ -992,6 +1027,23 @@ cudaError_t launch_part_probe(const ExpandArgs& a, const uint32_t* succ, uint64_
   return cudaGetLastError();
 }
 
+// The queued level kernel as a second choice: 4-word vectors, one lane per bucket
+// of at most 8 words (with larger buckets it measured slower than the plain one).
+template <int W, int B, int G>
+constexpr bool kSecondQueued = W == 4 && G == 1 && B <= 8;
+
+using ExpandLauncher = cudaError_t (*)(const ExpandArgs&, int, size_t, cudaStream_t);
+template <int W, int B, int G>
+ExpandLauncher queued_launcher() {
+  if constexpr (kSecondQueued<W, B, G>) return &launch_expand<W, B, G, true>;
+  else return nullptr;
+}
+template <int W, int B, int G>
+const void* queued_fn() {
+  if constexpr (kSecondQueued<W, B, G>) return reinterpret_cast<const void*>(&gxd::expand_kernel<W, B, G, true>);
+  else return nullptr;
+}
+
 template <int W, int B, int G>
 const KernelSet* kernel_set() {
   static const KernelSet ks{&launch_expand<W, B, G>,
@@ -1006,7 +1058,9 @@ const KernelSet* kernel_set() {
                             reinterpret_cast<const void*>(&gxd::part_count_kernel<W>),
                             reinterpret_cast<const void*>(&gxd::part_scatter_kernel<W>),
                             reinterpret_cast<const void*>(&gxd::part_probe_kernel<W, B, G>),
-                            reinterpret_cast<const void*>(&gxd::init_kernel<W, B, G>)};
+                            reinterpret_cast<const void*>(&gxd::init_kernel<W, B, G>),
+                            queued_launcher<W, B, G>(),
+                            queued_fn<W, B, G>()};
   return &ks;
 }
 

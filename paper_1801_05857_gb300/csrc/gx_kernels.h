@@ -69,10 +69,15 @@ struct ExpandArgs {
   // gx_explore_opts.region_passes).  region_mask = 0: one pass, no filter.
   uint64_t region_mask, region_bits;
   int count_states;          // 1: this pass counts transitions, deadlocks and violations
-  // GPU-wide cache of recently seen vectors (1- and 2-word vectors): 2^k entries of
-  // 64 bits in global memory, small enough to stay in L2; nullptr = off
+  // GPU-wide cache of recently seen vectors: 2^k entries of 64 bits in global
+  // memory, small enough to stay in L2; nullptr = off.  An entry holds a vector's
+  // 64-bit key: the vector itself for 1- and 2-word vectors, its payload bits
+  // packed for 4-word vectors whose fields take at most 64 bits (gkey_shift).
   unsigned long long* gcache;
   uint64_t gcache_mask;
+  // 4-word vectors: bit offset in the key of the payload of words 1, 2, 3
+  // (word 0 at offset 0; 64 = the word carries no field)
+  uint32_t gkey_shift[3];
 };
 
 // Partitioned expansion of one level (or one batch of it): successors are
@@ -131,6 +136,10 @@ struct KernelSet {
   const void* part_scatter_fn;
   const void* part_probe_fn;
   const void* init_fn;    // for graph kernel nodes
+  // the level kernel with the per-warp successor queue, where it is a second
+  // kernel (4-word vectors, one lane per bucket of at most 8 words); else nullptr
+  cudaError_t (*expand_queued)(const ExpandArgs&, int grid, size_t smem, cudaStream_t);
+  const void* expand_queued_fn;
 };
 
 // Kernels for slot width W, bucket words B and group lanes G; nullptr if the

@@ -107,13 +107,21 @@ gx_status gx_explore_noalloc(const gx_net* h, const gx_explore_opts* opts, void*
   while (fcap < fwant) fcap *= 2;
   // caches of seen vectors, as gx_explore chooses them (gx_explore_opts)
   uint64_t gentries = 0;
+  uint32_t gkey[3] = {64, 64, 64};
+  const bool key_fits = W <= 2 || gx::cache_key_shifts(net, gkey);
   if (o->global_cache_log2 == 0xFFFFFFFFu) {
     if (W <= 2 && G == 1 && (table_bytes / (4ull * W)) >= (1ull << 26)) gentries = 1ull << 23;
   } else if (o->global_cache_log2) {
     if (o->global_cache_log2 > 26) return gx::fail(GX_ERR_INVALID, "global_cache_log2 must be at most 26");
-    if (W <= 2) gentries = 1ull << o->global_cache_log2;
+    if (key_fits) gentries = 1ull << o->global_cache_log2;
   }
-  const uint32_t warp_log2 = o->warp_cache_log2 == 0xFFFFFFFFu ? (gentries ? 0u : 9u) : o->warp_cache_log2;
+  if (regions > nb) regions = (uint32_t)nb;
+  // the level kernel, as gx_explore chooses it: the queued second kernel with region passes
+  const bool queued = regions > 1 && ks->expand_queued;
+  const auto expand = queued ? ks->expand_queued : ks->expand;
+  const void* expand_fn = queued ? ks->expand_queued_fn : ks->expand_fn;
+  const uint32_t warp_log2 =
+      o->warp_cache_log2 == 0xFFFFFFFFu ? (gentries ? 0u : queued ? 6u : 9u) : o->warp_cache_log2;
   const uint64_t off_ctl = 0;
   const uint64_t off_blob = align256(sizeof(gx::Ctl));
   const uint64_t off_front = align256(off_blob + 4ull * net.blob.size());
@@ -149,7 +157,6 @@ gx_status gx_explore_noalloc(const gx_net* h, const gx_explore_opts* opts, void*
 
   int log2nb = 0;
   while ((1ull << log2nb) < nb) ++log2nb;
-  if (regions > nb) regions = (uint32_t)nb;
   int log2r = 0;
   while ((1u << log2r) < regions) ++log2r;
   gx::InitArgs ia{};
@@ -178,6 +185,7 @@ gx_status gx_explore_noalloc(const gx_net* h, const gx_explore_opts* opts, void*
   ea.count_states = 1;
   ea.gcache = gcache;
   ea.gcache_mask = gentries ? gentries - 1 : 0;
+  for (int w = 0; w < 3; ++w) ea.gkey_shift[w] = gkey[w];
   if (o->watch) {  // the safety check: violations counted and digested, not stored
     const uint32_t wp = o->watch_proc;
     ea.watch = 1;
@@ -205,9 +213,9 @@ gx_status gx_explore_noalloc(const gx_net* h, const gx_explore_opts* opts, void*
                                           " bytes of shared memory per CTA, more than " +
                                           std::to_string(smem_optin));
   }
-  NA_CUDA(cudaFuncSetAttribute(ks->expand_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  NA_CUDA(cudaFuncSetAttribute(expand_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks->expand_fn, gx::kBlock, smem));
+  NA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, expand_fn, gx::kBlock, smem));
   if (per_sm < 1) return gx::fail(GX_ERR_INVALID, "expansion kernel does not fit on an SM");
   if (o->ctas_per_sm) per_sm = std::min<int>(per_sm, (int)o->ctas_per_sm);
   const uint64_t max_grid = (uint64_t)sms * per_sm;
@@ -232,7 +240,7 @@ gx_status gx_explore_noalloc(const gx_net* h, const gx_explore_opts* opts, void*
       eq.region_bits = (uint64_t)q << (log2nb - log2r);
       eq.count_states = q == 0 ? 1 : 0;
       NA_CUDA(cudaMemsetAsync(&ctl->claim, 0, sizeof(unsigned long long), st));
-      NA_CUDA(ks->expand(eq, grid, smem, st));
+      NA_CUDA(expand(eq, grid, smem, st));
     }
     NA_CUDA(cudaMemcpyAsync(&hc, ctl, sizeof(gx::Ctl), cudaMemcpyDeviceToHost, st));
     NA_CUDA(cudaStreamSynchronize(st));

@@ -202,6 +202,24 @@ def test_mid_config_against_stored_oracle(cuda, bucket):
     assert s["fill"] <= 0.75
 
 
+def test_large_irregular_network_with_the_global_cache(cuda):
+    """The same 1.08e8-state network (16 fields of 4 bits: a 64-bit cache key) with
+    the GPU-wide cache (2^23 entries) and two region passes: exact against the stored
+    oracle values, with fewer bucket reads than without the cache."""
+    g = _golden_case("large3_network.json")
+    net = inputs.random_network(**g["generator"])
+    runs = {}
+    for log2 in (0, 23):
+        h, s, lv, ws = run_gpu(net, table_bytes=4 << 30, bucket_words=16, hash_rounds=32, region_passes=2,
+                               global_cache_log2=log2, warp_cache_log2=0)
+        assert s["global_cache_entries"] == (1 << log2 if log2 else 0)
+        assert (s["states"], s["transitions"], lv) == (g["states"], g["transitions"], g["levels"])
+        assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])
+        runs[log2] = s["probes"]
+        del ws
+    assert runs[23] < runs[0]
+
+
 def _part_nets():
     return [inputs.token_ring(11),
             inputs.random_network(0, 13, 64, 1, 3, 16, n_sync=8, parties=3, cluster=4),
@@ -408,7 +426,9 @@ def test_global_cache_keeps_results_exact(cuda, net, log2, host_loop):
     assert s["global_cache_entries"] == (1 << log2 if log2 else 0)
 
 
-def test_global_cache_reads_fewer_buckets_and_ignores_4_word_vectors(cuda):
+def test_global_cache_reads_fewer_buckets_and_ignores_wide_4_word_vectors(cuda):
+    """Fewer bucket reads with the cache; 4-word vectors whose fields take more than
+    64 bits (13 processes x 6 bits) have no 64-bit key and run without it."""
     net = inputs.random_network(1, 10, 16, 1, 3, 12, n_sync=4, parties=2, cluster=4)
     base = assert_parity(net, table_bytes=1 << 25, global_cache_log2=0, warp_cache_log2=0)
     with_cache = assert_parity(net, table_bytes=1 << 25, global_cache_log2=20, warp_cache_log2=0)
@@ -416,6 +436,67 @@ def test_global_cache_reads_fewer_buckets_and_ignores_4_word_vectors(cuda):
     s4 = assert_parity(inputs.random_network(0, 13, 64, 1, 3, 16, n_sync=8, parties=3, cluster=4),
                        table_bytes=1 << 25, global_cache_log2=20)
     assert s4["slot_words"] == 4 and s4["global_cache_entries"] == 0
+
+
+@pytest.mark.parametrize("log2", [4, 12, 20])
+@pytest.mark.parametrize("bucket,group", [(16, 1), (32, 8)])
+@pytest.mark.parametrize("net", [
+    inputs.random_network(1, 15, 16, 1, 3, 16, n_sync=8, parties=3, cluster=4),   # 60 field bits
+    inputs.product_network(1, 16, 16, [2] * 12 + [3] * 4)],                        # 64 field bits
+    ids=lambda n: n.name)
+def test_global_cache_keeps_4_word_results_exact(cuda, net, log2, bucket, group):
+    """4-word vectors (3 words of fields) whose fields fit 64 bits use the GPU-wide
+    cache with their field bits packed into one key; with one lane per bucket and
+    with 8 lanes per 32-word bucket, the results equal the oracle's."""
+    s = assert_parity(net, table_bytes=1 << 25, bucket_words=bucket, group_lanes=group,
+                      global_cache_log2=log2, warp_cache_log2=0)
+    assert s["slot_words"] == 4 and s["group_lanes"] == group
+    assert s["global_cache_entries"] == 1 << log2
+
+
+@pytest.mark.parametrize("bucket", [4, 8])
+@pytest.mark.parametrize("passes", [2, 4])
+@pytest.mark.parametrize("caches", [dict(), dict(warp_cache_log2=0), dict(global_cache_log2=20, warp_cache_log2=0),
+                                    dict(global_cache_log2=12, warp_cache_log2=4)], ids=["auto", "none", "global", "both"])
+def test_queued_four_word_kernel_is_exact(cuda, bucket, passes, caches):
+    """The level kernel with the per-warp successor queue for 4-word slots (one lane per
+    bucket of 4 or 8 words, region passes), with and without the caches of seen
+    vectors: every count, level and digest equals the oracle's and the closed forms."""
+    blocks = [2] * 12 + [3] * 4
+    net = inputs.product_network(1, 16, 16, blocks)
+    S, T = _product_closed_form(net, blocks)
+    s = assert_parity(net, table_bytes=1 << 25, bucket_words=bucket, group_lanes=1, hash_rounds=32,
+                      region_passes=passes, **caches)
+    assert (s["states"], s["transitions"], s["slot_words"], s["region_passes"]) == (S, T, 4, passes)
+
+
+@pytest.mark.parametrize("host_loop", [1, 0])
+def test_queued_four_word_kernel_with_deadlocks_and_full_buckets(cuda, host_loop):
+    """A 4-word network with deadlocks in a table filled to 86 % (many vectors go
+    past their first bucket) through the queued kernel: exact."""
+    net = inputs.random_network(2, 12, [1000] * 12, 0, 2, 14, n_sync=5, parties=2)  # 224,532 states, 888 deadlocks
+    r = oracle.explore(net)
+    assert r.deadlock_count > 0
+    table = 1 << 12
+    while table * 9 // 10 < r.states * 16:
+        table *= 2
+    s = assert_parity(net, table_bytes=table, bucket_words=8, group_lanes=1, hash_rounds=64, region_passes=2,
+                      host_loop=host_loop)
+    assert s["slot_words"] == 4 and s["fill"] > 0.8
+
+
+def test_global_cache_never_holds_the_all_zero_key(cuda):
+    """The vector whose fields are all 0 packs to key 0, the value of an empty entry,
+    so it is never cached.  Here it is reachable (the product family reaches every
+    combination of block states from any start) but not the initial state: a hit on
+    an empty entry would drop it from the set."""
+    net = inputs.product_network(1, 16, 16, [2] * 12 + [3] * 4)
+    for p in net.procs:
+        p.initial = 1
+    S, T = _product_closed_form(net, [2] * 12 + [3] * 4)
+    s = assert_parity(net, table_bytes=1 << 25, global_cache_log2=20, warp_cache_log2=0)
+    assert (s["states"], s["transitions"]) == (S, T)
+    assert s["global_cache_entries"] == 1 << 20
 
 
 def test_global_cache_is_cleared_between_searches(cuda):
@@ -436,23 +517,45 @@ def test_global_cache_is_cleared_between_searches(cuda):
         assert (s["states"], s["transitions"], gx.levels(h)) == (r.states, r.transitions, r.levels)
 
 
-@pytest.mark.parametrize("bucket,passes", [(16, 1), (8, 2), (32, 4)])
-def test_large_irregular_network_against_stored_oracle(cuda, bucket, passes):
+@pytest.mark.parametrize("bucket,group,passes", [(16, 0, 1), (8, 0, 2), (32, 0, 4), (8, 1, 1), (8, 1, 2), (4, 1, 4)])
+def test_large_irregular_network_against_stored_oracle(cuda, bucket, group, passes):
     """16 processes x 16 local states (3-word vectors in 4-word slots), 3-party rules
     on 10 % of the labels that shape the reachable set (1.08e8 states, 3.5 times as
     many as without the rule edges): states, transitions, every level, the deadlock
     digest and the digest of the whole set equal the oracle's, written by
-    tests/golden/make_golden.py; with one, two and four region passes."""
+    tests/golden/make_golden.py; with one, two and four region passes, one lane per
+    slot (group 0: the default) or one lane per bucket (with region passes, 4- and
+    8-word buckets of 4-word slots run the level kernel with the successor queue)."""
     g = _golden_case("large3_network.json")
     net = inputs.random_network(**g["generator"])
-    h, s, lv, ws = run_gpu(net, table_bytes=4 << 30, bucket_words=bucket, hash_rounds=32, region_passes=passes)
+    h, s, lv, ws = run_gpu(net, table_bytes=4 << 30, bucket_words=bucket, group_lanes=group, hash_rounds=32,
+                           region_passes=passes)
     assert s["slot_words"] == 4 and s["region_passes"] == passes
+    assert s["group_lanes"] == (group or bucket // 4)
     assert (s["states"], s["transitions"]) == (g["states"], g["transitions"])
     assert lv == g["levels"]
     assert (s["deadlock_count"], s["deadlock_sum"], s["deadlock_xor"]) == (
         g["deadlock_count"], g["deadlock_sum"], g["deadlock_xor"])
     assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])
     assert s["fill"] <= 0.75
+
+
+def test_large_irregular_network_with_the_global_cache(cuda):
+    """The same 1.08e8-state network (16 fields of 4 bits: a 64-bit cache key) with
+    the GPU-wide cache (2^23 entries) and two region passes: exact against the stored
+    oracle values, with fewer bucket reads than without the cache."""
+    g = _golden_case("large3_network.json")
+    net = inputs.random_network(**g["generator"])
+    runs = {}
+    for log2 in (0, 23):
+        h, s, lv, ws = run_gpu(net, table_bytes=4 << 30, bucket_words=16, hash_rounds=32, region_passes=2,
+                               global_cache_log2=log2, warp_cache_log2=0)
+        assert s["global_cache_entries"] == (1 << log2 if log2 else 0)
+        assert (s["states"], s["transitions"], lv) == (g["states"], g["transitions"], g["levels"])
+        assert gx.set_digest(h, ws) == (g["states"], g["set_sum"], g["set_xor"])
+        runs[log2] = s["probes"]
+        del ws
+    assert runs[23] < runs[0]
 
 
 @pytest.mark.parametrize("host_loop", [1, 0])

@@ -23,6 +23,7 @@ def _nets():
         inputs.workload("tiny"),                                                # 1-word vectors
         inputs.token_ring(11),                                                  # 2-word vectors
         inputs.random_network(0, 13, 64, 1, 3, 16, n_sync=8, parties=3, cluster=4),  # 4-word
+        inputs.random_network(1, 15, 16, 1, 3, 16, n_sync=8, parties=3, cluster=4),  # 4-word, 60 bits
         inputs.random_network(6, 4, 5, 0, 2, 6, n_sync=2, parties=2),           # has deadlocks
     ]
 
