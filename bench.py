@@ -68,8 +68,9 @@ def parse():
     ap.add_argument("--no-table", action="store_true", help="skip the Sec. 5.1 find-or-put part")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload part")
     ap.add_argument("--no-guided", action="store_true", help="skip the guided deadlock-search part")
+    ap.add_argument("--probe-gib", type=int, default=128, help="--experiment probe-sweep: buffer size in GiB")
     ap.add_argument("--experiment", default="", choices=["", "table-sweep", "cuckoo-sweep", "bucket-sweep", "scaled", "scaling-table", "scorer", "batch",
-                             "guided", "cache-sweep", "guided-compare", "search"],
+                             "guided", "cache-sweep", "guided-compare", "search", "probe-sweep"],
                     help="table-sweep: Sec. 5.1 duplication x bucket sweep; bucket-sweep: the "
                          "exploration for every (bucket, group) size; scaled: one large token ring; "
                          "scaling-table: ring and producer/consumer families by size (Table 1); "
@@ -309,6 +310,49 @@ def random_access_ceiling(torch, gx, ws, s: dict) -> dict:
     out["note"] = ("32-byte reads, 4 in flight per thread, 8 CTAs of 256 threads per SM; the rate is the same "
                    "at every depth and occupancy measured (profiles/random_access_roofline.md)")
     return out
+
+
+def probe_sweep(torch, gx, gib: int) -> None:
+    """The random-read ceiling on one allocation of `gib` GiB (gx_probe_gather, 2^28 reads a
+    launch, best of three after a warm-up): launch shape on 4 GiB, unit size, windows of the
+    allocation, and page locality across all of it.  One JSON line per point."""
+    buf = torch.zeros(gib << 28, dtype=torch.int32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st = torch.cuda.current_stream()
+    n = 1 << 28
+    gw = 1 << 28  # words per GiB
+
+    def point(part, off_gib, span_gib, unit, load, k, ctas, g):
+        b = buf[off_gib * gw:(off_gib + span_gib) * gw]
+        used = gx.probe_gather(b, n, unit, load, k, ctas, g, 7, sink)
+        best = 1e30
+        for rep in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            gx.probe_gather(b, n, unit, load, k, ctas, g, 11 + rep, sink)
+            e1.record(st)
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        print(json.dumps({"experiment": "probe-sweep", "part": part, "offset_gib": off_gib, "span_gib": span_gib,
+                          "unit_bytes": unit, "load_bytes": load, "in_flight": k, "ctas_per_sm": used,
+                          "group_log2": g, "g_reads_per_s": round(n / best / 1e6, 2),
+                          "g_sectors_per_s": round(n * max(1, load // 32) / best / 1e6, 2)}), flush=True)
+
+    for load in (4, 32):
+        for ctas in (1, 8):
+            for k in (1, 2, 4, 8, 16, 32):
+                if load == 32 and k == 32:
+                    continue
+                point("launch shape", 0, 4, 32, load, k, ctas, 0)
+    for span in (4, 64, gib):
+        for unit in (32, 64, 128):
+            point("unit size", 0, span, unit, unit, 2, 8, 0)
+    for off, span in ((0, 4), (64, 4), (gib - 4, 4), (0, 32), (gib - 32, 32), (0, 64), (gib - 64, 64), (0, gib)):
+        if off + span <= gib:
+            point("window", off, span, 32, 4, 8, 8, 0)
+    for g in (12, 16, 21, 24, 27, 30, 33):
+        if (1 << g) < gib << 30:
+            point("locality", 0, gib, 32, 4, 8, 8, g)
 
 
 def table_keys(torch, n: int, dup: int, seed: int = 0):
@@ -1126,6 +1170,8 @@ def run_experiment(args):
                           "explored": s["explored"], "transitions": s["transitions"], "probes": s["probes"],
                           "region_passes": s["region_passes"], "fill": round(s["fill"], 4),
                           "algorithmic_bytes": bytes_alg, "gpu_ms": round(s["gpu_ms"], 3)}), flush=True)
+    elif args.experiment == "probe-sweep":
+        probe_sweep(torch, gx, args.probe_gib)
     elif args.experiment == "cache-sweep":
         # per-warp cache x GPU-wide cache sizes on --workload (device level loop), median of
         # --steps searches after --warmup

@@ -604,14 +604,15 @@ gx_status gx_probe_random(uint32_t kind, uint32_t* buffer, uint64_t words, uint6
 
 /* Random gathers with a chosen launch shape and locality, for measuring the
  * ceiling the table's random accesses are held against (no counterpart in the
- * paper).  Over the largest power-of-two number of unit_bytes-sized units (32
- * or 64) that fits `words` uint32 of `buffer`, `n` accesses at counter-based
- * pseudo-random unit positions (mix64(seed + i), as gx_probe_random):
+ * paper).  Over the largest power-of-two number of unit_bytes-sized units (32,
+ * 64 or 128: one sector, or the bucket sizes of 16 and 32 words) that fits
+ * `words` uint32 of `buffer`, `n` accesses at counter-based pseudo-random unit
+ * positions (mix64(seed + i), as gx_probe_random):
  *   load_bytes:  4 = read one word of the unit (the DRAM still moves the whole
  *                sector; one register per access in flight), or unit_bytes =
  *                read the whole unit with 256-bit loads;
  *   in_flight:   accesses each thread issues before it uses any: 1, 2, 4, 8,
- *                16, or 32 (4-byte loads only);
+ *                16, or 32 (4-byte loads only); at most 4 with 128-byte loads;
  *   ctas_per_sm: 256-thread CTAs per SM, 1..8, lowered to what the kernel's
  *                registers allow; *ctas_used (host, may be NULL) gets the
  *                value launched (the grid is SMs x ctas_used);

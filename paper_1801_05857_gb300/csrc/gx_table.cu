@@ -357,13 +357,15 @@ gx_status gx_probe_gather(uint32_t* buffer, uint64_t words, uint64_t n, uint32_t
   gx::clear_error();
   if (!buffer || !sink) return gx::fail(GX_ERR_INVALID, "NULL device pointer");
   if (reinterpret_cast<uintptr_t>(buffer) % 256) return gx::fail(GX_ERR_INVALID, "buffer is not 256-byte aligned");
-  if (unit_bytes != 32 && unit_bytes != 64) return gx::fail(GX_ERR_INVALID, "unit_bytes must be 32 or 64");
+  if (unit_bytes != 32 && unit_bytes != 64 && unit_bytes != 128)
+    return gx::fail(GX_ERR_INVALID, "unit_bytes must be 32, 64 or 128");
   if (load_bytes != 4 && load_bytes != unit_bytes)
     return gx::fail(GX_ERR_INVALID, "load_bytes must be 4 or unit_bytes");
   const int K = (int)in_flight;
   if (K != 1 && K != 2 && K != 4 && K != 8 && K != 16 && K != 32)
     return gx::fail(GX_ERR_INVALID, "in_flight must be 1, 2, 4, 8, 16 or 32");
   if (load_bytes > 4 && K > 16) return gx::fail(GX_ERR_INVALID, "in_flight above 16 only with 4-byte loads");
+  if (load_bytes > 64 && K > 4) return gx::fail(GX_ERR_INVALID, "in_flight above 4 only with loads of at most 64 bytes");
   if (ctas_per_sm < 1 || ctas_per_sm > 8) return gx::fail(GX_ERR_INVALID, "ctas_per_sm must be 1..8");
   const int unit_words = (int)unit_bytes / 4;
   if ((uint64_t)unit_words > words) return gx::fail(GX_ERR_INVALID, "buffer smaller than one access");
@@ -371,7 +373,7 @@ gx_status gx_probe_gather(uint32_t* buffer, uint64_t words, uint64_t n, uint32_t
   while (n_units * 2 * unit_words <= words) n_units *= 2;
   uint32_t gbits = 0;
   if (group_log2) {
-    uint32_t ub = unit_bytes == 32 ? 5 : 6;
+    uint32_t ub = unit_bytes == 32 ? 5 : unit_bytes == 64 ? 6 : 7;
     if (group_log2 < ub) return gx::fail(GX_ERR_INVALID, "group_log2 smaller than one unit");
     gbits = group_log2 - ub;
     if ((1ull << gbits) > n_units) return gx::fail(GX_ERR_INVALID, "locality group larger than the buffer");
@@ -385,6 +387,7 @@ gx_status gx_probe_gather(uint32_t* buffer, uint64_t words, uint64_t n, uint32_t
   GX_SWEEP(1, 1) GX_SWEEP(2, 1) GX_SWEEP(4, 1) GX_SWEEP(8, 1) GX_SWEEP(16, 1) GX_SWEEP(32, 1)
   GX_SWEEP(1, 8) GX_SWEEP(2, 8) GX_SWEEP(4, 8) GX_SWEEP(8, 8) GX_SWEEP(16, 8)
   GX_SWEEP(1, 16) GX_SWEEP(2, 16) GX_SWEEP(4, 16) GX_SWEEP(8, 16) GX_SWEEP(16, 16)
+  GX_SWEEP(1, 32) GX_SWEEP(2, 32) GX_SWEEP(4, 32)
 #undef GX_SWEEP
   if (!f) return gx::fail(GX_ERR_INVALID, "no such probe shape");
   fn = reinterpret_cast<const void*>(f);
