@@ -353,6 +353,22 @@ def probe_sweep(torch, gx, gib: int) -> None:
     for g in (12, 16, 21, 24, 27, 30, 33):
         if (1 << g) < gib << 30:
             point("locality", 0, gib, 32, 4, 8, 8, g)
+    # random compare-and-swap of 32-, 64- and 128-bit slots (the table's insertions; last,
+    # since it writes the buffer)
+    for span in (4, min(64, gib)):
+        b = buf[:span * gw]
+        for nbytes in (4, 8, 16):
+            gx.probe_random(1, b, n, nbytes, 5, sink)
+            best = 1e30
+            for rep in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                gx.probe_random(1, b, n, nbytes, 21 + rep, sink)
+                e1.record(st)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            print(json.dumps({"experiment": "probe-sweep", "part": "cas", "offset_gib": 0, "span_gib": span,
+                              "unit_bytes": nbytes, "g_cas_per_s": round(n / best / 1e6, 2)}), flush=True)
 
 
 def table_keys(torch, n: int, dup: int, seed: int = 0):
