@@ -173,7 +173,9 @@ typedef struct gx_explore_opts {
                                     memory (2^(n-1) for 4-word vectors, the same bytes), a hit
                                     skips find-or-put.  0 = off, 1..12 = 2^n, 0xFFFFFFFF =
                                     automatic (gx_default_opts): 2^9 unless the GPU-wide
-                                    cache below is in use (together they measured slower) */
+                                    cache below is in use (together they measured slower);
+                                    2^6 with the queued 4-word kernel (region_passes), whose
+                                    CTAs then still fit 5 per SM */
   float guided_scale;            /* GX_DL_GUIDED: score at which a state falls in the last
                                     bin (scores are predicted distances / max_dist); 0 = 1.0 */
   uint32_t watch;                /* 1 = safety check (Sec. 3: the negation of a safety property
@@ -200,9 +202,15 @@ typedef struct gx_explore_opts {
                                     One pass's random table reads then stay inside one
                                     region: on GB300 random reads run at the full rate
                                     within any 64 GiB and 4x slower across 128 GiB
-                                    (address-translation reach).  Results do not depend on
-                                    it.  0 = auto: the fewest passes whose regions are at
-                                    most 64 GiB (1 for tables up to 64 GiB) */
+                                    (address-translation reach).  In a table above 64 GiB
+                                    every hash round of a vector stays inside the 64 GiB
+                                    span of its first bucket, so later rounds stay in the
+                                    pass's region too.  With more than one pass, 4-word
+                                    slots in 4- or 8-word buckets with one lane per bucket
+                                    run the level kernel with the successor queue (only the
+                                    pass's successors are probed, 32 at a time).  Results
+                                    do not depend on it.  0 = auto: the fewest passes whose
+                                    regions are at most 64 GiB (1 for tables up to 64 GiB) */
   uint32_t global_cache_log2;    /* GPU-wide cache of recently seen vectors: 2^n
                                     direct-mapped 64-bit entries in the workspace, cleared at
                                     the start of each search and small enough to stay in L2.
