@@ -93,7 +93,7 @@ def parse():
 # bucket, hash rounds.  The memory-scaled network fills 62.5 % of a 128 GiB table.
 WORKLOAD_SETTINGS = {
     "scaled": dict(table_log2_words=35, bucket=8, group=1, rounds=64),
-    "scaled90": dict(table_log2_words=35, bucket=32, group=1, rounds=64),
+    "scaled90": dict(table_log2_words=35, bucket=16, group=1, rounds=64),
     "mid": dict(table_log2_words=28, bucket=8, group=1, rounds=32),
     "tiny": dict(table_log2_words=16, bucket=32, group=1, rounds=8),
 }
