@@ -450,6 +450,19 @@ def test_global_cache_keeps_results_exact(cuda, net, log2, host_loop):
     assert s["global_cache_entries"] == (1 << log2 if log2 else 0)
 
 
+@pytest.mark.parametrize("passes", [2, 4])
+@pytest.mark.parametrize("net", [inputs.token_ring(11), inputs.workload("tiny"),
+                                 inputs.random_network(1, 10, 16, 1, 3, 12, n_sync=4, parties=2, cluster=4)],
+                         ids=lambda n: n.name)
+def test_global_cache_with_region_passes(cuda, net, passes):
+    """1- and 2-word vectors with the GPU-wide cache and region passes together (the
+    queued kernel filters by region first, then by the cache; every pass reads the cache
+    that earlier passes filled): exact against the oracle."""
+    s = assert_parity(net, table_bytes=1 << 25, bucket_words=8, group_lanes=1, region_passes=passes,
+                      global_cache_log2=20, warp_cache_log2=0)
+    assert s["region_passes"] == passes and s["global_cache_entries"] == 1 << 20
+
+
 def test_global_cache_reads_fewer_buckets_and_ignores_wide_4_word_vectors(cuda):
     """Fewer bucket reads with the cache; 4-word vectors whose fields take more than
     64 bits (13 processes x 6 bits) have no 64-bit key and run without it."""
