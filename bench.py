@@ -290,25 +290,39 @@ def random_access_ceiling(torch, gx, ws, s: dict) -> dict:
     table_words = s["table_slots"] * s["slot_words"]
     regions = s["region_passes"]
 
-    def rate(b, seed):
-        gx.probe_gather(b, n, 32, 32, 4, 8, 0, seed, sink)
+    def rate(b, seed, probe):
+        probe(b, seed)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         for k in range(3):
-            gx.probe_gather(b, n, 32, 32, 4, 8, 0, seed + 1 + k, sink)
+            probe(b, seed + 1 + k)
         e1.record(st)
         torch.cuda.synchronize()
         return n / (e0.elapsed_time(e1) / 3 * 1e-3) / 1e9
 
+    def persistent(b, seed):  # a grid that fits on the SMs at once, as the level kernel's does
+        gx.probe_gather(b, n, 32, 32, 4, 8, 0, seed, sink)
+
+    def turnover(b, seed):  # more CTAs than fit at once: the faster mode of the memory system
+        gx.probe_random(0, b, n, 32, seed, sink)
+
+    def waves(b, seed):  # the same gather as the ceiling, from a grid of 16 CTAs per SM
+        gx.probe_gather(b, n, 32, 32, 4, 16, 0, seed, sink)
+
     span_t = min(span, 1 << (table_words.bit_length() - 1))
-    out["independent_g_per_s"] = round(rate(buf[:span_t], 101), 3)
+    out["independent_g_per_s"] = round(rate(buf[:span_t], 101, persistent), 3)
     out["span_gib"] = round(4 * span_t / 2 ** 30, 2)
     region_words = span_t // regions
+    region = buf[:region_words]
     out["region_gib"] = round(4 * region_words / 2 ** 30, 2)
-    out["in_region_g_per_s"] = round(rate(buf[:region_words], 201), 3) if regions > 1 else out["independent_g_per_s"]
+    out["in_region_g_per_s"] = round(rate(region, 201, persistent), 3) if regions > 1 else out["independent_g_per_s"]
     out["ceiling_g_per_s"] = out["in_region_g_per_s"]
-    out["note"] = ("32-byte reads, 4 in flight per thread, 8 CTAs of 256 threads per SM; the rate is the same "
-                   "at every depth and occupancy measured (profiles/random_access_roofline.md)")
+    out["best_in_region_g_per_s"] = round(max(out["in_region_g_per_s"], rate(region, 301, turnover),
+                                              rate(region, 401, waves)), 3)
+    out["note"] = ("ceiling: 32-byte reads, 4 in flight per thread, a grid resident on the SMs at once (the "
+                   "level kernel's launch style; the same rate at every depth and occupancy measured); best: "
+                   "the highest rate any probe reached on the same region, from a grid with more CTAs than "
+                   "fit at once (profiles/random_access_roofline.md)")
     return out
 
 
@@ -347,12 +361,34 @@ def probe_sweep(torch, gx, gib: int) -> None:
     for span in (4, 64, gib):
         for unit in (32, 64, 128):
             point("unit size", 0, span, unit, unit, 2, 8, 0)
+    # a grid resident at once (the level kernel's launch style) against grids of more CTAs
+    # than fit, whose CTAs finish and start during the launch
+    for span in (4, min(64, gib)):
+        for k in (1, 4):
+            for ctas in (8, 12, 16, 32):
+                point("grid waves", 0, span, 32, 32, k, ctas, 0)
     for off, span in ((0, 4), (64, 4), (gib - 4, 4), (0, 32), (gib - 32, 32), (0, 64), (gib - 64, 64), (0, gib)):
         if off + span <= gib:
             point("window", off, span, 32, 4, 8, 8, 0)
     for g in (12, 16, 21, 24, 27, 30, 33):
         if (1 << g) < gib << 30:
             point("locality", 0, gib, 32, 4, 8, 8, g)
+    # the same gathers through gx_probe_random (one fixed shape: 8 CTAs per SM, 4 reads in
+    # flight per thread for 16- and 32-byte units, 2 for 64 and 128)
+    for span in (4, min(64, gib)):
+        b = buf[:span * gw]
+        for nbytes in (32, 64, 128):
+            gx.probe_random(0, b, n, nbytes, 3, sink)
+            best = 1e30
+            for rep in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                gx.probe_random(0, b, n, nbytes, 31 + rep, sink)
+                e1.record(st)
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            print(json.dumps({"experiment": "probe-sweep", "part": "probe_random", "offset_gib": 0, "span_gib": span,
+                              "unit_bytes": nbytes, "g_reads_per_s": round(n / best / 1e6, 2)}), flush=True)
     # random compare-and-swap of 32-, 64- and 128-bit slots (the table's insertions; last,
     # since it writes the buffer)
     for span in (4, min(64, gib)):
@@ -802,6 +838,8 @@ def run_ours(args, world, rank, local, pg):
         roof["random_access"] = random_access_ceiling(torch, gx, ws, s)
         roof["probes_per_s_ceiling"] = roof["random_access"]["ceiling_g_per_s"]
         roof["frac_of_random_gather32"] = round(roof["probes_per_s"] / roof["random_access"]["ceiling_g_per_s"], 4)
+        roof["frac_of_best_random_gather32"] = round(
+            roof["probes_per_s"] / roof["random_access"]["best_in_region_g_per_s"], 4)
         # the other level loop on the same workload and workspace
         alt = search_opts(gx, args, host_loop=args.level_loop != "host")
         gx.explore(h, alt, ws)

@@ -621,9 +621,11 @@ gx_status gx_probe_random(uint32_t kind, uint32_t* buffer, uint64_t words, uint6
  *                read the whole unit with 256-bit loads;
  *   in_flight:   accesses each thread issues before it uses any: 1, 2, 4, 8,
  *                16, or 32 (4-byte loads only); at most 4 with 128-byte loads;
- *   ctas_per_sm: 256-thread CTAs per SM, 1..8, lowered to what the kernel's
- *                registers allow; *ctas_used (host, may be NULL) gets the
- *                value launched (the grid is SMs x ctas_used);
+ *   ctas_per_sm: 256-thread CTAs per SM: 1..8, lowered to what the kernel's
+ *                registers allow (a grid resident at once); 9..32 as asked (a
+ *                grid of more than one wave, whose CTAs finish and start during
+ *                the launch); *ctas_used (host, may be NULL) gets the value
+ *                launched (the grid is SMs x ctas_used);
  *   group_log2:  0 = every access independent; g >= log2(unit_bytes) = the
  *                accesses a warp issues together (32 x in_flight) fall in one
  *                randomly chosen aligned block of 2^g bytes (page locality).

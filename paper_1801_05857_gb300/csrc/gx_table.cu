@@ -366,7 +366,7 @@ gx_status gx_probe_gather(uint32_t* buffer, uint64_t words, uint64_t n, uint32_t
     return gx::fail(GX_ERR_INVALID, "in_flight must be 1, 2, 4, 8, 16 or 32");
   if (load_bytes > 4 && K > 16) return gx::fail(GX_ERR_INVALID, "in_flight above 16 only with 4-byte loads");
   if (load_bytes > 64 && K > 4) return gx::fail(GX_ERR_INVALID, "in_flight above 4 only with loads of at most 64 bytes");
-  if (ctas_per_sm < 1 || ctas_per_sm > 8) return gx::fail(GX_ERR_INVALID, "ctas_per_sm must be 1..8");
+  if (ctas_per_sm < 1 || ctas_per_sm > 32) return gx::fail(GX_ERR_INVALID, "ctas_per_sm must be 1..32");
   const int unit_words = (int)unit_bytes / 4;
   if ((uint64_t)unit_words > words) return gx::fail(GX_ERR_INVALID, "buffer smaller than one access");
   uint64_t n_units = 1;
@@ -394,7 +394,10 @@ gx_status gx_probe_gather(uint32_t* buffer, uint64_t words, uint64_t n, uint32_t
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, gx::kBlock, 0);
   if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
-  const int ctas = (int)ctas_per_sm < per_sm ? (int)ctas_per_sm : (per_sm > 0 ? per_sm : 1);
+  // up to 8: lowered to what fits at once (a resident grid); above 8: as asked, so the
+  // grid runs in more than one wave
+  const int ctas = ctas_per_sm > 8 ? (int)ctas_per_sm
+                                   : ((int)ctas_per_sm < per_sm ? (int)ctas_per_sm : (per_sm > 0 ? per_sm : 1));
   if (ctas_used) *ctas_used = (uint32_t)ctas;
   if (n == 0) return GX_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

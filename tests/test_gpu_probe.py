@@ -47,15 +47,16 @@ def expected_checksum(words: int, n: int, unit_bytes: int, load_bytes: int, k: i
 @pytest.mark.parametrize("unit,load,k", [(32, 4, 1), (32, 32, 4), (64, 64, 2), (64, 4, 8),
                                          (128, 128, 1), (128, 128, 4), (128, 4, 16)])
 @pytest.mark.parametrize("group_log2", [0, 12])
-def test_probe_gather_reads_the_documented_positions(cuda, unit, load, k, group_log2):
+@pytest.mark.parametrize("ctas", [2, 24])
+def test_probe_gather_reads_the_documented_positions(cuda, unit, load, k, group_log2, ctas):
     import torch
     words = 1 << 20
     buf = torch.arange(words, dtype=torch.int32, device="cuda")
     sink = torch.zeros(1, dtype=torch.int64, device="cuda")
     n, seed = 5000, 12345
-    used = gx.probe_gather(buf, n, unit, load, k, 2, group_log2, seed, sink)
+    used = gx.probe_gather(buf, n, unit, load, k, ctas, group_log2, seed, sink)
     torch.cuda.synchronize()
-    assert 1 <= used <= 2
+    assert (1 <= used <= 2) if ctas <= 8 else used == ctas
     assert int(sink.item()) == expected_checksum(words, n, unit, load, k, group_log2, seed)
 
 
@@ -64,7 +65,7 @@ def test_probe_gather_rejects_shapes_it_does_not_build(cuda):
     buf = torch.zeros(1 << 16, dtype=torch.int32, device="cuda")
     sink = torch.zeros(1, dtype=torch.int64, device="cuda")
     for args in ((48, 48, 1, 1, 0), (128, 128, 8, 1, 0), (32, 16, 1, 1, 0), (64, 64, 32, 1, 0),
-                 (32, 32, 3, 1, 0), (32, 32, 1, 9, 0), (128, 128, 1, 1, 6)):
+                 (32, 32, 3, 1, 0), (32, 32, 1, 33, 0), (32, 32, 1, 0, 0), (128, 128, 1, 1, 6)):
         unit, load, k, ctas, g = args
         with pytest.raises(gx.GxError):
             gx.probe_gather(buf, 100, unit, load, k, ctas, g, 1, sink)
