@@ -74,6 +74,29 @@ def test_noalloc_safety_check_matches_oracle(cuda, stop):
         assert got["transitions"] == r.transitions
 
 
+@pytest.mark.parametrize("bucket", [4, 8])
+@pytest.mark.parametrize("passes", [2, 4])
+@pytest.mark.parametrize("net", [
+    inputs.random_network(1, 15, 16, 1, 3, 16, n_sync=8, parties=3, cluster=4),   # 4-word, 60 field bits
+    inputs.random_network(2, 12, [1000] * 12, 0, 2, 14, n_sync=5, parties=2)],    # 4-word, deadlocks
+    ids=lambda n: n.name)
+def test_noalloc_region_passes_with_one_lane_per_bucket(cuda, net, bucket, passes):
+    """4-word slots in 4- or 8-word buckets, one lane per bucket, with region passes: the
+    entry point runs the level kernel with the successor queue, as gx_explore does; twice
+    in a row, exact against the oracle."""
+    import torch
+    r = oracle.explore(net)
+    h = gx.load_network(net)
+    opts = gx.default_opts(table_bytes=32 << 20, bucket_words=bucket, group_lanes=1, hash_rounds=32,
+                           region_passes=passes)
+    for _ in range(2):
+        got, levels = gx.explore_noalloc(h, opts)
+        torch.cuda.synchronize()
+        assert {k: got[k] for k in _oracle_fields(r)} == _oracle_fields(r)
+        assert levels == r.levels
+        assert got["region_passes"] == passes and got["slot_words"] == 4
+
+
 def test_noalloc_rejects_what_it_cannot_do(cuda):
     h = gx.load_network(inputs.token_ring(6))
     with pytest.raises(gx.GxError) as e:
