@@ -206,6 +206,20 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": mx, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def kernel_code_digest(paths) -> str:
+    """sha256 of kernel sources with // comments and blank lines removed: a capture stays
+    valid across comment edits and is voided by any change to the code."""
+    import hashlib
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p)) as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
+    return h.hexdigest()
+
+
 def ncu_traffic(args, s: dict, probes: int, launches: int) -> dict | None:
     """DRAM bytes per launch of the expansion kernel from a committed one-kernel ncu
     capture (profiles/expand_kernel_<workload>_traffic.json), used when it was taken on
@@ -213,7 +227,6 @@ def ncu_traffic(args, s: dict, probes: int, launches: int) -> dict | None:
     capture of a smaller table than this run's (the size rule for counter captures) is
     scaled by algorithmic bytes: its DRAM bytes per algorithmic byte times this run's
     algorithmic bytes per launch."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", f"expand_kernel_{args.workload}_traffic.json")
     if not os.path.exists(path):
         return None
@@ -222,8 +235,7 @@ def ncu_traffic(args, s: dict, probes: int, launches: int) -> dict | None:
     cfg = t.get("config", {})
     if (cfg.get("bucket"), cfg.get("group"), cfg.get("warp_cache")) != (args.bucket, args.group, args.warp_cache):
         return None
-    src = b"".join(open(os.path.join(ROOT, p), "rb").read() for p in t["kernel_sources"])
-    if hashlib.sha256(src).hexdigest() != t["kernel_sources_sha256"]:
+    if kernel_code_digest(t["kernel_sources"]) != t["kernel_code_sha256"]:
         return None
     if "dram_bytes_per_search" in t and cfg.get("table_log2_words") == args.table_log2_words \
             and cfg.get("region_passes", 1) == s["region_passes"]:

@@ -545,10 +545,12 @@ struct WarpQueue {
 // A lane holds min(G, 4) first buckets in flight of B / G words each; up to
 // 8 such words fit 48 registers (5 CTAs), up to 16 fit 64 (4 CTAs), more get
 // 85 (3 CTAs); 4-word slots with 4 or more lanes per bucket also get 3.
-// (Checked with -Xptxas -v: at most a few bytes spill.  4-word slots in
-// 16-word buckets spill 48 bytes at 48 registers and ran slower there.)  The
-// level kernel is latency-bound, so the extra CTA pays: 4-word slots in 8-word
-// buckets explore the memory-scaled network in 4.49 s at 5 CTAs, 4.94 s at 4.
+// (Checked with -Xptxas -v: at most a few bytes spill; the queued kernel for
+// 4-word slots in 8-word buckets spills 48 bytes and is still the fastest
+// there.  4-word slots in 16-word buckets spill 48 bytes at 48 registers and
+// ran slower.)  The level kernel is latency-bound, so the extra CTA pays: 4-word
+// slots in 8-word buckets explore the memory-scaled network in 4.49 s at 5
+// CTAs, 4.94 s at 4 (plain kernel).
 template <int W, int B, int G>
 struct ExpandOcc {
   static constexpr int inflight = (G < 4 ? G : 4) * (B / G);
@@ -562,7 +564,8 @@ struct ExpandOcc {
 // for 1- and 2-word vectors with one lane per bucket; for 4-word vectors in 4-
 // and 8-word buckets it is a second kernel, chosen when region passes discard
 // most successors (memory-scaled network, 2 passes: 3.52 s queued against 4.48 s;
-// large3 network in 4 GiB, 1 pass: 57.8 ms queued against 49.4 ms).
+// the 1.08e8-state irregular network in 4 GiB, 1 pass: 57.8 ms queued against
+// 49.4 ms).
 template <int W, int B, int G, bool Q = (G == 1 && W <= 2)>
 __global__ void __launch_bounds__(gx::kBlock, ExpandOcc<W, B, G>::min_ctas) expand_kernel(const gx::ExpandArgs a) {
   static_assert(!Q || G == 1, "the successor queue needs one lane per bucket");
