@@ -547,8 +547,9 @@ struct WarpQueue {
 // 85 (3 CTAs); 4-word slots with 4 or more lanes per bucket also get 3.
 // (Checked with -Xptxas -v: at most a few bytes spill; the queued kernel for
 // 4-word slots in 8-word buckets spills 48 bytes and is still the fastest
-// there.  4-word slots in 16-word buckets spill 48 bytes at 48 registers and
-// ran slower.)  The level kernel is latency-bound, so the extra CTA pays: 4-word
+// there: 3.50 s on the memory-scaled network against 3.76 s at 4 CTAs and 64
+// registers.  4-word slots in 16-word buckets spill 48 bytes at 48 registers
+// and ran slower.)  The level kernel is latency-bound, so the extra CTA pays: 4-word
 // slots in 8-word buckets explore the memory-scaled network in 4.49 s at 5
 // CTAs, 4.94 s at 4 (plain kernel).
 template <int W, int B, int G>
