@@ -897,7 +897,7 @@ def run_ours(args, world, rank, local, pg):
         rp = random_access_peak(torch, gx)
         g32 = rp["gather32_per_s"]
         pts = []
-        for dup, bucket, group in ((1, 16, 2), (21, 8, 2)):
+        for dup, bucket, group in ((1, 8, 1), (21, 8, 1)):
             nd = n - n % dup
             keys = table_keys(torch, nd, dup)
             pts.append(table_point(torch, gx, keys, nd, dup, 1, 1 << 27, bucket, group, 32, g32))

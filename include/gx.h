@@ -556,7 +556,9 @@ gx_status gx_explore_noalloc(const gx_net* net, const gx_explore_opts* opts, voi
  *            key, 0 = the key was already present, 2 = no free slot in any round.
  *   counters: device pointer to 3 uint64 (inserted, found, failed), added to.
  * key_words: 1, 2 or 4; bucket_words, group_lanes, hash_rounds as in
- * gx_explore_opts (0 = default).  Asynchronous on `stream`. */
+ * gx_explore_opts (0 = default).  The keys are taken by a grid-stride loop on
+ * 16 times the CTAs that fit at once (random reads run faster from such a grid
+ * than from a resident one).  Asynchronous on `stream`. */
 gx_status gx_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t key_words,
                          uint32_t bucket_words, uint32_t group_lanes, uint32_t hash_rounds,
                          uint32_t* table, uint64_t table_words, uint8_t* result,
