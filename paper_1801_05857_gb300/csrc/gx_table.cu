@@ -310,7 +310,9 @@ gx_status gx_cuckoo_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t 
       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gxd::cuckoo_kernel<2>, gx::kBlock, 0);
   if (e != cudaSuccess) return gx::fail(GX_ERR_CUDA, cudaGetErrorString(e));
   const uint64_t blocks_needed = (n_keys + gx::kBlock - 1) / gx::kBlock;
-  const uint64_t cap = (uint64_t)sm_count() * (per_sm > 0 ? per_sm : 1);
+  // the same grid as gx_find_or_put's (16 times the CTAs that fit at once), so that the
+  // comparison of the two tables is on equal terms
+  const uint64_t cap = (uint64_t)sm_count() * (per_sm > 0 ? per_sm : 1) * 16;
   const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
   if (key_words == 1) gxd::cuckoo_kernel<1><<<grid > 0 ? grid : 1, gx::kBlock, 0, st>>>(a);
   else gxd::cuckoo_kernel<2><<<grid > 0 ? grid : 1, gx::kBlock, 0, st>>>(a);
