@@ -595,8 +595,9 @@ gx_status gx_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t key_wor
  *             dropped a key.
  *   counters: device, 4 uint64 (inserted, found, failed, exchanges), added to.
  * n_hash 2..8 (0 = 4); max_chain 1..4096 (0 = 128).  GX_ERR_INVALID for other
- * values, an even multiplier, NULL or misaligned pointers.  Asynchronous on
- * `stream`. */
+ * values, an even multiplier, NULL or misaligned pointers.  One thread per key,
+ * on the same grid shape as gx_find_or_put (16 times the CTAs that fit at
+ * once).  Asynchronous on `stream`. */
 gx_status gx_cuckoo_find_or_put(const uint32_t* keys, uint64_t n_keys, uint32_t key_words,
                                 uint32_t n_hash, uint32_t max_chain, const uint64_t* muls,
                                 uint32_t* table, uint64_t table_slots, uint8_t* result,
